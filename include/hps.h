@@ -1,0 +1,189 @@
+/*
+ * hps.h -- C ABI of the GB300 (sm_103a) library for the iterative HPS
+ * Helmholtz solver of arXiv:2112.02211.
+ *
+ * Problem (1.1) of the paper, on the unit cube (0,1)^3:
+ *
+ *     -Lap u - kappa^2 (1 - b(x)) u = s(x)   in (0,1)^3,
+ *     du/dn + i eta u              = t(x)   on the boundary,      Re(eta) != 0.
+ *
+ * The cube is split into nx x ny x nz equal leaf boxes (Sec. 2).  Each leaf
+ * carries the modified Chebyshev collocation grid of order p (Sec. 2.1) and
+ * q x q Gauss-Legendre points on each of its six faces, q = p - 2.  The
+ * library solves the face form of the HPS system: the unknowns are the
+ * incoming impedance data f = du/dn + i eta u on every leaf face (Definition
+ * in Sec. 2.2), and
+ *
+ *     (I + Pi R) f = tbar - Pi h                                        (*)
+ *
+ * where R = blockdiag(R^tau) holds the leaf impedance-to-impedance (ItI)
+ * maps, h^tau the leaf's outgoing response to the body load s, and Pi the
+ * swap of outgoing data across shared faces (the interface condition
+ * f^alpha = -g^beta, eq. (inter)); tbar is t on boundary faces, 0 elsewhere.
+ * (*) is the exact reduction of the paper's global system (Sec. 3.1) onto
+ * face data.  It is solved by restarted GMRES, right-preconditioned by a
+ * block-Jacobi preconditioner over 2x2x2 leaf clusters built from locally
+ * homogenized leaf maps (Sec. 4, Sec. 4.1).
+ *
+ * Layouts (all complex numbers are interleaved (re, im) pairs):
+ *   leaf tau = ix + nx*(iy + ny*iz)                       (Fig. 4(a))
+ *   face k in 0..5 = -x, +x, -y, +y, -z, +z               (Fig. 2, eq. (flux))
+ *   face vector  [rhs][leaf][face][j2][j1], j1 fastest; in-face axes:
+ *                +-x faces -> (y, z), +-y -> (x, z), +-z -> (x, y).
+ *                N_f = nx*ny*nz*6*q*q complex values per right-hand side.
+ *   interior     [rhs][leaf][k][j][i], i (x) fastest, n1 = p - 2 points per
+ *                axis, i.e. nx*ny*nz*n1^3 values per right-hand side, at the
+ *                interior Chebyshev nodes returned by hps_nodes.
+ *
+ * Errors: every entry point returns HPS_OK (0) or a negative HPS_E* code and
+ * never throws; hps_last_error() gives a message for the calling thread.
+ * Ownership: the handle owns all device state it allocates (leaf maps,
+ * preconditioner blocks, Krylov workspace).  Callers own every buffer they
+ * pass in.  A handle is used by one host thread at a time.
+ */
+#ifndef HPS_H
+#define HPS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPS_OK 0
+#define HPS_EINVAL (-1)      /* bad argument: sizes, q != p-2, Re(eta) == 0, NaN/Inf input */
+#define HPS_ENOMEM (-2)      /* device allocation failed or over the HBM budget */
+#define HPS_ECUDA (-3)       /* a CUDA call failed (message in hps_last_error) */
+#define HPS_ENOCONV (-4)     /* GMRES hit maxit; the best iterate and info are still written */
+#define HPS_EBREAKDOWN (-5)  /* singular pivot or non-finite value in a kernel */
+#define HPS_ETIMEOUT (-6)    /* a bounded device wait gave up */
+
+/* Element types of device vectors passed to hps_apply / hps_precond. */
+#define HPS_C128 0 /* complex double, 16 bytes */
+#define HPS_C64 1  /* complex float, 8 bytes */
+
+/* Solve forms (bit flags for hps_options.forms). */
+#define HPS_FORM_FP64 1  /* everything in complex FP64 */
+#define HPS_FORM_MIXED 2 /* complex-FP32 apply/preconditioner inside FP64 Krylov + FP64 outer residual */
+
+typedef struct hps_handle hps_handle;
+
+/* Leaves per axis and Chebyshev order; q must equal p - 2, 4 <= p <= 16. */
+typedef struct {
+  int nx, ny, nz;
+  int p;
+  int q;
+} hps_grid;
+
+typedef struct {
+  int forms;          /* HPS_FORM_* flags: which operator precisions hps_setup builds */
+  int restart;        /* GMRES restart length m (default 50) */
+  int cluster;        /* block-Jacobi cluster width in leaves per axis: 2 (default) or 0 = none */
+  int maxit;          /* maximum inner iterations per solve (default 5000) */
+  int max_rhs;        /* maximum right-hand sides per solve (default 1) */
+  size_t hbm_budget;  /* bytes the handle may allocate; 0 = no limit */
+  int device;         /* CUDA device ordinal */
+} hps_options;
+
+typedef struct {
+  int iterations;      /* inner GMRES iterations (max over right-hand sides) */
+  int cycles;          /* restart cycles, each ending with an FP64 true residual */
+  int converged;       /* 1 when every right-hand side met the tolerance */
+  double rel_residual; /* max over RHS of ||b - A f||_2 / ||b||_2, FP64 operator */
+  double seconds;      /* wall time of the solve (RHS build + GMRES), host clock */
+} hps_solve_info;
+
+/* Fills *opt with the defaults listed above (forms = HPS_FORM_FP64|HPS_FORM_MIXED). */
+void hps_default_options(hps_options* opt);
+
+/*
+ * Node coordinates of a grid, computed on the device (Sec. 2.1).
+ * interior_xyz: host, nx*ny*nz*n1^3*3 doubles (x,y,z per node, layout above),
+ * face_xyz:     host, N_f*3 doubles, the Gauss points of every leaf face.
+ * Either pointer may be NULL.  Uses the current CUDA device.
+ */
+int hps_nodes(const hps_grid* grid, double* interior_xyz, double* face_xyz);
+
+/*
+ * Builds the leaf ItI maps R^tau (Gauss basis), the body-load maps H^tau and
+ * the preconditioner for one medium.  Per leaf this assembles the leaf system
+ * of eq. (leaf) and eliminates it with partial pivoting in FP64 on the
+ * device: R_C = I - 2 i eta (A^{-1})_bb, H_C = -2 i eta (A^{-1})_bi, then
+ * R = P R_C P^{-1}, H = P H_C with P the Chebyshev-to-Gauss face
+ * interpolation.  The preconditioner uses the same construction with
+ * C = kappa^2 (1 - b) replaced by lambda^tau = (max + min)/2 of C over the
+ * leaf's interior nodes (Sec. 4.1, real and imaginary parts separately).
+ *
+ * b: host, nx*ny*nz*n1^3 complex (interleaved doubles), b at the interior
+ *    nodes of hps_nodes.  kappa real, eta complex given as (eta, 0): the
+ *    imaginary part of eta is 0 in this interface.  opt may be NULL.
+ * On success *out owns all device state; free it with hps_destroy.
+ */
+int hps_setup(const hps_grid* grid, double kappa, double eta, const double* b,
+              const hps_options* opt, hps_handle** out);
+
+/*
+ * y = (I + Pi R) f for nrhs right-hand sides (the operator of (*); Sec. 2.2,
+ * Sec. 3.1).  f, y: device, nrhs*N_f complex of the given dtype (HPS_C128
+ * needs HPS_FORM_FP64 operators, HPS_C64 needs HPS_FORM_MIXED ones), must not
+ * overlap.  stream: a cudaStream_t (NULL = legacy default stream).  The call
+ * is asynchronous with respect to the host.
+ */
+int hps_apply(hps_handle* h, int dtype, const void* f, void* y, int nrhs, void* stream);
+
+/*
+ * z = J^{-1} r, the cluster block-Jacobi preconditioner (Sec. 4, Algorithm 4
+ * in face form): on each cluster c of 2x2x2 leaves, z_c = (I + Pi_c R~)^{-1} r_c
+ * where R~ are the homogenized leaf maps and Pi_c swaps only across faces
+ * inside the cluster.  Same argument rules as hps_apply.  Uses a scratch
+ * buffer owned by the handle, so calls on one handle must not overlap.
+ */
+int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream);
+
+/*
+ * Right-hand side of (*): b = tbar - Pi h with h^tau = H^tau s^tau.
+ * s: nrhs interior vectors or NULL (s = 0); t: nrhs face vectors or NULL
+ * (t = 0; only boundary-face entries are read).  s, t, b_out: device,
+ * complex double.
+ */
+int hps_rhs(hps_handle* h, const double* s, const double* t, int nrhs, double* b_out,
+            void* stream);
+
+/*
+ * Solves (*) for nrhs right-hand sides to ||b - A f||_2 <= tol ||b||_2 per
+ * right-hand side, with the FP64 operator.  form: HPS_FORM_FP64 (restarted
+ * GMRES in FP64) or HPS_FORM_MIXED (complex-FP32 apply and preconditioner
+ * inside an FP64 Krylov basis, with the true residual recomputed in FP64 at
+ * every restart, which restores FP64 accuracy).  s, t as in hps_rhs; f_out:
+ * nrhs*N_f complex doubles.  Pointers may be host or device memory (detected
+ * per pointer; host buffers are copied inside the call).  info may be NULL.
+ * The call returns after the result is in f_out.
+ */
+int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs,
+                    double tol, double* f_out, hps_solve_info* info, void* stream);
+
+/* What hps_export copies out (host doubles, interleaved complex). */
+#define HPS_EXPORT_R 0      /* R^index, 6q^2 x 6q^2 row-major, FP64 */
+#define HPS_EXPORT_H 1      /* H^index, 6q^2 x n1^3 row-major */
+#define HPS_EXPORT_LAMBDA 2 /* lambda^index: one complex value */
+#define HPS_EXPORT_KC 3     /* K_c of cluster index, n_int x n_int row-major */
+#define HPS_EXPORT_B 4      /* B^index: leaf index's (internal rows x external cols) block of R~ */
+/* Copies one leaf's (or cluster's) operator to host memory for inspection.
+ * Returns the number of doubles written (>0) or a negative error code;
+ * with host_out == NULL only the size is returned. */
+long long hps_export(hps_handle* h, int what, int index, double* host_out);
+
+/* Device bytes held by the handle. */
+size_t hps_memory_bytes(const hps_handle* h);
+
+/* Frees all device state of the handle (NULL is accepted). */
+int hps_destroy(hps_handle* h);
+
+/* Message of the last failure on the calling thread ("" when none). */
+const char* hps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPS_H */

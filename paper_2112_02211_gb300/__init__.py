@@ -1,0 +1,186 @@
+"""GB300-native iterative HPS Helmholtz solver (arXiv:2112.02211), Python binding.
+
+The compute path is the CUDA library ``libhps.so`` (C ABI in include/hps.h);
+this module only marshals arguments: device buffers are torch tensors on the
+GPU, streams are torch streams.  There is no CPU fallback: every call runs
+the library's kernels and raises ``HPSError`` when the library or the GPU is
+missing.
+
+    import paper_2112_02211_gb300 as hps
+    xi, xf = hps.nodes(16, 16, 16, p=10)             # interior / face points
+    solver = hps.Solver(16, 16, 16, p=10, kappa=40.0, eta=40.0, b=b_at_xi)
+    f, info = solver.solve(s=s_at_xi, tol=1e-6, form="mixed")
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+from ._native import HPSError
+
+__all__ = ["Solver", "nodes", "face_normals", "HPSError", "load"]
+
+load = N.load
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def nodes(nx, ny, nz, p):
+    """Interior Chebyshev nodes (nl, n1^3, 3) and face Gauss points (nl, 6, q^2, 3), from the device."""
+    lib = N.load()
+    q = p - 2
+    nl = nx * ny * nz
+    xi = np.zeros((nl, (p - 2) ** 3, 3))
+    xf = np.zeros((nl, 6, q * q, 3))
+    g = N.Grid(nx, ny, nz, p, q)
+    N.check(lib.hps_nodes(ctypes.byref(g), xi.ctypes.data_as(ctypes.c_void_p), xf.ctypes.data_as(ctypes.c_void_p)))
+    return xi, xf
+
+
+def face_normals():
+    """Outward unit normal of face k = -x, +x, -y, +y, -z, +z."""
+    n = np.zeros((6, 3))
+    for k in range(6):
+        n[k, k // 2] = -1.0 if k % 2 == 0 else 1.0
+    return n
+
+
+_FORMS = {"fp64": N.HPS_FORM_FP64, "mixed": N.HPS_FORM_MIXED}
+
+
+class Solver:
+    """One medium on one grid: leaf ItI maps, preconditioner and Krylov workspace on the GPU."""
+
+    def __init__(self, nx, ny, nz, p, kappa, eta=None, b=None, forms=("fp64", "mixed"), restart=50,
+                 cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0):
+        self.lib = N.load()
+        self.nx, self.ny, self.nz, self.p, self.q = nx, ny, nz, p, p - 2
+        self.nl = nx * ny * nz
+        self.ni = (p - 2) ** 3
+        self.nb = 6 * self.q * self.q
+        self.nf = self.nl * self.nb
+        self.kappa = float(kappa)
+        self.eta = float(kappa if eta is None else eta)
+        self.max_rhs = max_rhs
+        grid = N.Grid(nx, ny, nz, p, p - 2)
+        opt = N.Options()
+        self.lib.hps_default_options(ctypes.byref(opt))
+        opt.forms = sum(_FORMS[f] for f in forms)
+        opt.restart = restart
+        opt.cluster = cluster
+        opt.maxit = maxit
+        opt.max_rhs = max_rhs
+        opt.hbm_budget = hbm_budget
+        opt.device = device
+        bb = None
+        if b is not None:
+            bb = np.ascontiguousarray(np.asarray(b, dtype=np.complex128).reshape(-1))
+            if bb.size != self.nl * self.ni:
+                raise ValueError("b must hold one value per interior node")
+        h = ctypes.c_void_p()
+        N.check(self.lib.hps_setup(ctypes.byref(grid), self.kappa, self.eta,
+                                   None if bb is None else bb.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(opt), ctypes.byref(h)))
+        self.handle = h
+
+    # -- operators on device tensors ---------------------------------------------------------
+    def _nrhs(self, t):
+        n = t.numel()
+        if n % self.nf:
+            raise ValueError("face vectors must hold a multiple of N_f values")
+        return n // self.nf
+
+    def apply(self, f, out=None, stream=None):
+        """y = (I + Pi R) f; f complex128 (FP64 maps) or complex64 (FP32 maps) on the GPU."""
+        torch = _torch()
+        dt = N.HPS_C128 if f.dtype == torch.complex128 else N.HPS_C64
+        y = torch.empty_like(f) if out is None else out
+        N.check(self.lib.hps_apply(self.handle, dt, _ptr(f), _ptr(y), self._nrhs(f), _stream(stream)))
+        return y
+
+    def precond(self, r, out=None, stream=None):
+        """z = J^{-1} r (cluster block Jacobi with homogenized leaf maps)."""
+        torch = _torch()
+        dt = N.HPS_C128 if r.dtype == torch.complex128 else N.HPS_C64
+        z = torch.empty_like(r) if out is None else out
+        N.check(self.lib.hps_precond(self.handle, dt, _ptr(r), _ptr(z), self._nrhs(r), _stream(stream)))
+        return z
+
+    def rhs(self, s=None, t=None, nrhs=1, stream=None):
+        """b = tbar - Pi (H s) on the GPU (complex128 tensors)."""
+        torch = _torch()
+        out = torch.empty(nrhs * self.nf, dtype=torch.complex128, device="cuda")
+        N.check(self.lib.hps_rhs(self.handle, _ptr(s), _ptr(t), nrhs, _ptr(out), _stream(stream)))
+        return out
+
+    def solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=None, out=None, stream=None):
+        """Solve (I + Pi R) f = tbar - Pi H s.  s, t, out: torch tensors (device or host) or numpy
+        arrays (host).  Returns (f, info dict)."""
+        torch = _torch()
+
+        def as_arg(a):
+            if a is None:
+                return None, None
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a.astype(np.complex128, copy=False))
+                return a, a.ctypes.data_as(ctypes.c_void_p)
+            return a, _ptr(a)
+
+        if nrhs is None:
+            if s is not None:
+                nrhs = int(np.prod(s.shape)) // (self.nl * self.ni)
+            elif t is not None:
+                nrhs = int(np.prod(t.shape)) // self.nf
+            else:
+                nrhs = 1
+        if out is None:
+            out = torch.empty(nrhs * self.nf, dtype=torch.complex128, device="cuda")
+        s_keep, s_ptr = as_arg(s)
+        t_keep, t_ptr = as_arg(t)
+        o_keep, o_ptr = as_arg(out)
+        info = N.SolveInfo()
+        rc = self.lib.hps_gmres_solve(self.handle, _FORMS[form], s_ptr, t_ptr, nrhs, float(tol), o_ptr,
+                                      ctypes.byref(info), _stream(stream))
+        if rc not in (N.HPS_OK, N.HPS_ENOCONV):
+            N.check(rc)
+        d = {"iterations": info.iterations, "cycles": info.cycles, "converged": bool(info.converged),
+             "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc}
+        return out, d
+
+    def export(self, what, index):
+        """Copy one stored operator block to the host (numpy complex128)."""
+        codes = {"R": N.HPS_EXPORT_R, "H": N.HPS_EXPORT_H, "lambda": N.HPS_EXPORT_LAMBDA,
+                 "Kc": N.HPS_EXPORT_KC, "B": N.HPS_EXPORT_B}
+        n = N.check(self.lib.hps_export(self.handle, codes[what], index, None))
+        buf = np.zeros(n // 2, dtype=np.complex128)
+        N.check(self.lib.hps_export(self.handle, codes[what], index, buf.ctypes.data_as(ctypes.c_void_p)))
+        return buf
+
+    @property
+    def memory_bytes(self):
+        return self.lib.hps_memory_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.hps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

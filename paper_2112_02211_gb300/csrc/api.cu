@@ -1,0 +1,458 @@
+// C ABI of the HPS library (declared in include/hps.h).  Argument checks,
+// allocation of the handle's device state, and dispatch to the kernels of
+// setup.cu, apply.cu and krylov.cu.  Nothing here throws across the ABI.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+cudaError_t launch_cdiag(const double2* b, double kappa, long long count, double2* c, cudaStream_t st);
+
+}  // namespace hps
+
+using namespace hps;
+
+namespace {
+
+int validate_grid(const hps_grid* g) {
+  if (!g) {
+    set_error("grid is NULL");
+    return HPS_EINVAL;
+  }
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nx > 4096 || g->ny > 4096 || g->nz > 4096) {
+    set_error("leaf counts per axis must be in 1..4096");
+    return HPS_EINVAL;
+  }
+  if ((long long)g->nx * g->ny * g->nz > (1LL << 22)) {
+    set_error("too many leaves");
+    return HPS_EINVAL;
+  }
+  if (g->p < 4 || g->p > 16) {
+    set_error("Chebyshev order p must be in 4..16");
+    return HPS_EINVAL;
+  }
+  if (g->q != g->p - 2) {
+    set_error("q must equal p - 2 (square Chebyshev-to-Gauss face interpolation)");
+    return HPS_EINVAL;
+  }
+  return HPS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int dalloc(hps_handle* h, void** p, size_t bytes) {
+  bytes = bytes ? bytes : 16;
+  if (h->opt.hbm_budget && h->bytes + bytes > h->opt.hbm_budget) {
+    set_error("allocation exceeds the HBM budget of the handle");
+    return HPS_ENOMEM;
+  }
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    return HPS_ENOMEM;
+  }
+  h->bytes += bytes;
+  return HPS_OK;
+}
+
+void free_handle(hps_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  krylov_free(h);
+  void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->lambda, h->Kc64, h->Kc32, h->B64, h->B32, h->pc_scratch,
+                  h->dct.slot_lf, h->dct.slot_cluster, h->dct.cl_slot_begin, h->dct.cl_kc_off, h->dct.lf_slot,
+                  h->dct.int_mask, h->dct.b_off};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int check_finite(const double* v, long long n, const char* what) {
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) {
+      set_error(std::string(what) + " contains NaN or Inf");
+      return HPS_EINVAL;
+    }
+  return HPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hps_default_options(hps_options* o) {
+  if (!o) return;
+  o->forms = HPS_FORM_FP64 | HPS_FORM_MIXED;
+  o->restart = 50;
+  o->cluster = 2;
+  o->maxit = 5000;
+  o->max_rhs = 1;
+  o->hbm_budget = 0;
+  o->device = 0;
+}
+
+const char* hps_last_error(void) { return g_err.c_str(); }
+
+int hps_nodes(const hps_grid* g, double* xi, double* xf) {
+  int rc = validate_grid(g);
+  if (rc) return rc;
+  TableLayout tl(g->p);
+  const long long nl = (long long)g->nx * g->ny * g->nz;
+  const long long ni = (long long)(g->p - 2) * (g->p - 2) * (g->p - 2), nb = 6LL * g->q * g->q;
+  double *T = nullptr, *dxi = nullptr, *dxf = nullptr;
+  auto cleanup = [&]() {
+    if (T) cudaFree(T);
+    if (dxi) cudaFree(dxi);
+    if (dxf) cudaFree(dxf);
+  };
+  auto body = [&]() -> int {
+    HPS_CUDA_TRY(cudaMalloc(&T, tl.total * sizeof(double)));
+    if (xi) HPS_CUDA_TRY(cudaMalloc(&dxi, nl * ni * 3 * sizeof(double)));
+    if (xf) HPS_CUDA_TRY(cudaMalloc(&dxf, nl * nb * 3 * sizeof(double)));
+    HPS_CUDA_TRY(launch_tables(T, tl, 1.0 / g->nx, 1.0 / g->ny, 1.0 / g->nz, 0));
+    HPS_CUDA_TRY(launch_nodes(T, tl, g->nx, g->ny, g->nz, dxi, dxf, 0));
+    if (xi) HPS_CUDA_TRY(cudaMemcpy(xi, dxi, nl * ni * 3 * sizeof(double), cudaMemcpyDeviceToHost));
+    if (xf) HPS_CUDA_TRY(cudaMemcpy(xf, dxf, nl * nb * 3 * sizeof(double), cudaMemcpyDeviceToHost));
+    return HPS_OK;
+  };
+  rc = body();
+  cleanup();
+  return rc;
+}
+
+int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, const hps_options* opt,
+              hps_handle** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return HPS_EINVAL;
+  }
+  *out = nullptr;
+  int rc = validate_grid(g);
+  if (rc) return rc;
+  if (!std::isfinite(kappa) || !std::isfinite(eta) || eta == 0.0) {
+    set_error("kappa must be finite and eta finite with Re(eta) != 0");
+    return HPS_EINVAL;
+  }
+  hps_options o;
+  hps_default_options(&o);
+  if (opt) o = *opt;
+  if (o.restart < 1 || o.restart > 60) {
+    set_error("restart must be in 1..60");
+    return HPS_EINVAL;
+  }
+  if (o.cluster != 0 && o.cluster != 2) {
+    set_error("cluster must be 0 (no preconditioner) or 2");
+    return HPS_EINVAL;
+  }
+  if (o.max_rhs < 1 || o.max_rhs > 1024 || o.maxit < 1 || !(o.forms & (HPS_FORM_FP64 | HPS_FORM_MIXED))) {
+    set_error("bad options (max_rhs, maxit or forms)");
+    return HPS_EINVAL;
+  }
+  hps_handle* h = new hps_handle();
+  h->opt = o;
+  h->dev = o.device;
+  h->nx = g->nx;
+  h->ny = g->ny;
+  h->nz = g->nz;
+  h->p = g->p;
+  h->q = g->q;
+  h->n1 = g->p - 2;
+  h->ni = h->n1 * h->n1 * h->n1;
+  h->nb = 6 * h->q * h->q;
+  h->n = h->ni + h->nb;
+  h->nl = g->nx * g->ny * g->nz;
+  h->nf = (long long)h->nl * h->nb;
+  h->nint = (long long)h->nl * h->ni;
+  h->kappa = kappa;
+  h->eta = eta;
+  h->h[0] = 1.0 / g->nx;
+  h->h[1] = 1.0 / g->ny;
+  h->h[2] = 1.0 / g->nz;
+  h->tl = TableLayout(g->p);
+  h->ldR = (int)rup4(h->nb);
+  h->ldH = (int)rup4(h->ni);
+  if (b && (rc = check_finite(b, 2 * h->nint, "b"))) {
+    delete h;
+    return rc;
+  }
+  double2 *db = nullptr, *dc = nullptr;
+  auto body = [&]() -> int {
+    HPS_CUDA_TRY(cudaSetDevice(h->dev));
+    HPS_CUDA_TRY(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
+    HPS_CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    cudaStream_t st = h->stream;
+    const bool want64 = (o.forms & HPS_FORM_FP64) != 0;
+    const bool want32 = (o.forms & HPS_FORM_MIXED) != 0;
+    int r;
+    if ((r = dalloc(h, (void**)&h->tables, h->tl.total * sizeof(double)))) return r;
+    const size_t rel = (size_t)h->nl * h->nb * h->ldR;
+    if ((r = dalloc(h, (void**)&h->R64, rel * sizeof(double2)))) return r;
+    if (want32 && (r = dalloc(h, (void**)&h->R32, rel * sizeof(float2)))) return r;
+    if ((r = dalloc(h, (void**)&h->H64, (size_t)h->nl * h->nb * h->ldH * sizeof(double2)))) return r;
+    if ((r = dalloc(h, (void**)&h->lambda, (size_t)h->nl * sizeof(double2)))) return r;
+    HPS_CUDA_TRY(cudaMemsetAsync(h->R64, 0, rel * sizeof(double2), st));
+    if (h->R32) HPS_CUDA_TRY(cudaMemsetAsync(h->R32, 0, rel * sizeof(float2), st));
+    HPS_CUDA_TRY(cudaMemsetAsync(h->H64, 0, (size_t)h->nl * h->nb * h->ldH * sizeof(double2), st));
+    HPS_CUDA_TRY(cudaMalloc(&db, (size_t)h->nint * sizeof(double2)));
+    HPS_CUDA_TRY(cudaMalloc(&dc, (size_t)h->nint * sizeof(double2)));
+    if (b)
+      HPS_CUDA_TRY(cudaMemcpyAsync(db, b, (size_t)h->nint * sizeof(double2), cudaMemcpyHostToDevice, st));
+    else
+      HPS_CUDA_TRY(cudaMemsetAsync(db, 0, (size_t)h->nint * sizeof(double2), st));
+    HPS_CUDA_TRY(launch_tables(h->tables, h->tl, h->h[0], h->h[1], h->h[2], st));
+    HPS_CUDA_TRY(launch_cdiag(db, kappa, h->nint, dc, st));
+    if ((r = build_exact_maps(h, dc, st))) return r;
+    if (o.cluster == 2) {
+      build_cluster_tables(h, 2);
+      h->has_precond = true;
+      const ClusterTables& ct = h->ct;
+      if (want64) {
+        if ((r = dalloc(h, (void**)&h->Kc64, std::max<long long>(1, ct.kc_elems) * sizeof(double2)))) return r;
+        if ((r = dalloc(h, (void**)&h->B64, std::max<long long>(1, ct.b_elems) * sizeof(double2)))) return r;
+        HPS_CUDA_TRY(cudaMemsetAsync(h->Kc64, 0, std::max<long long>(1, ct.kc_elems) * sizeof(double2), st));
+        HPS_CUDA_TRY(cudaMemsetAsync(h->B64, 0, std::max<long long>(1, ct.b_elems) * sizeof(double2), st));
+      }
+      if (want32) {
+        if ((r = dalloc(h, (void**)&h->Kc32, std::max<long long>(1, ct.kc_elems) * sizeof(float2)))) return r;
+        if ((r = dalloc(h, (void**)&h->B32, std::max<long long>(1, ct.b_elems) * sizeof(float2)))) return r;
+        HPS_CUDA_TRY(cudaMemsetAsync(h->Kc32, 0, std::max<long long>(1, ct.kc_elems) * sizeof(float2), st));
+        HPS_CUDA_TRY(cudaMemsetAsync(h->B32, 0, std::max<long long>(1, ct.b_elems) * sizeof(float2), st));
+      }
+      const size_t ts = std::max<size_t>(1, (size_t)ct.nslots * h->q * h->q) * o.max_rhs * sizeof(double2);
+      if ((r = dalloc(h, &h->pc_scratch, ts))) return r;
+      if ((r = build_preconditioner(h, dc, st))) return r;
+    }
+    HPS_CUDA_TRY(cudaStreamSynchronize(st));
+    return HPS_OK;
+  };
+  rc = body();
+  if (db) cudaFree(db);
+  if (dc) cudaFree(dc);
+  if (rc) {
+    free_handle(h);
+    return rc;
+  }
+  *out = h;
+  return HPS_OK;
+}
+
+int hps_apply(hps_handle* h, int dtype, const void* f, void* y, int nrhs, void* stream) {
+  if (!h || !f || !y || nrhs < 1) {
+    set_error("hps_apply: bad arguments");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == HPS_C128) {
+    HPS_CUDA_TRY(launch_apply(h, false, VType::C128, f, VType::C128, y, nullptr, nrhs, false, st));
+  } else if (dtype == HPS_C64) {
+    if (!h->R32) {
+      set_error("hps_apply: complex-FP32 operators were not built (HPS_FORM_MIXED)");
+      return HPS_EINVAL;
+    }
+    HPS_CUDA_TRY(launch_apply(h, true, VType::C64, f, VType::C64, y, nullptr, nrhs, false, st));
+  } else {
+    set_error("hps_apply: unknown dtype");
+    return HPS_EINVAL;
+  }
+  return HPS_OK;
+}
+
+int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream) {
+  if (!h || !r || !z || nrhs < 1) {
+    set_error("hps_precond: bad arguments");
+    return HPS_EINVAL;
+  }
+  if (nrhs > h->opt.max_rhs) {
+    set_error("hps_precond: nrhs exceeds options.max_rhs");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = (dtype == HPS_C128) ? sizeof(double2) : sizeof(float2);
+  if (dtype != HPS_C128 && dtype != HPS_C64) {
+    set_error("hps_precond: unknown dtype");
+    return HPS_EINVAL;
+  }
+  if (!h->has_precond) {
+    HPS_CUDA_TRY(cudaMemcpyAsync(z, r, (size_t)nrhs * h->nf * es, cudaMemcpyDeviceToDevice, st));
+    return HPS_OK;
+  }
+  if (dtype == HPS_C128) {
+    if (!h->Kc64) {
+      set_error("hps_precond: FP64 preconditioner was not built (HPS_FORM_FP64)");
+      return HPS_EINVAL;
+    }
+    HPS_CUDA_TRY(launch_precond(h, false, VType::C128, r, VType::C128, z, h->pc_scratch, nrhs, st));
+  } else {
+    if (!h->Kc32) {
+      set_error("hps_precond: FP32 preconditioner was not built (HPS_FORM_MIXED)");
+      return HPS_EINVAL;
+    }
+    HPS_CUDA_TRY(launch_precond(h, true, VType::C64, r, VType::C64, z, h->pc_scratch, nrhs, st));
+  }
+  return HPS_OK;
+}
+
+int hps_rhs(hps_handle* h, const double* s, const double* t, int nrhs, double* b_out, void* stream) {
+  if (!h || !b_out || nrhs < 1) {
+    set_error("hps_rhs: bad arguments");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  HPS_CUDA_TRY(launch_rhs(h, (const double2*)s, (const double2*)t, (double2*)b_out, nrhs, (cudaStream_t)stream));
+  return HPS_OK;
+}
+
+int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs, double tol, double* f_out,
+                    hps_solve_info* info, void* stream) {
+  if (!h || !f_out || nrhs < 1 || !(tol > 0.0)) {
+    set_error("hps_gmres_solve: bad arguments");
+    return HPS_EINVAL;
+  }
+  if (form != HPS_FORM_FP64 && form != HPS_FORM_MIXED) {
+    set_error("hps_gmres_solve: form must be HPS_FORM_FP64 or HPS_FORM_MIXED");
+    return HPS_EINVAL;
+  }
+  if (nrhs > h->opt.max_rhs) {
+    set_error("hps_gmres_solve: nrhs exceeds options.max_rhs");
+    return HPS_EINVAL;
+  }
+  if (form == HPS_FORM_MIXED && (!h->R32 || (h->has_precond && !h->Kc32))) {
+    set_error("hps_gmres_solve: mixed-form operators were not built");
+    return HPS_EINVAL;
+  }
+  if (form == HPS_FORM_FP64 && h->has_precond && !h->Kc64) {
+    set_error("hps_gmres_solve: FP64 preconditioner was not built");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  int rc = krylov_alloc(h, nrhs);
+  if (rc) return rc;
+  KrylovSpace& k = h->ks;
+  const double2* sd = (const double2*)s;
+  const double2* td = (const double2*)t;
+  if (s && !is_device_ptr(s)) {
+    if ((rc = check_finite(s, 2LL * nrhs * h->nint, "s"))) return rc;
+    if (!k.s_dev && (rc = dalloc(h, (void**)&k.s_dev, (size_t)h->opt.max_rhs * h->nint * sizeof(double2)))) return rc;
+    HPS_CUDA_TRY(cudaMemcpyAsync(k.s_dev, s, (size_t)nrhs * h->nint * sizeof(double2), cudaMemcpyHostToDevice, st));
+    sd = k.s_dev;
+  }
+  if (t && !is_device_ptr(t)) {
+    if ((rc = check_finite(t, 2LL * nrhs * h->nf, "t"))) return rc;
+    if (!k.t_dev && (rc = dalloc(h, (void**)&k.t_dev, (size_t)h->opt.max_rhs * h->nf * sizeof(double2)))) return rc;
+    HPS_CUDA_TRY(cudaMemcpyAsync(k.t_dev, t, (size_t)nrhs * h->nf * sizeof(double2), cudaMemcpyHostToDevice, st));
+    td = k.t_dev;
+  }
+  HPS_CUDA_TRY(launch_rhs(h, sd, td, k.b, nrhs, st));
+  const bool fdev = is_device_ptr(f_out);
+  double2* x = fdev ? (double2*)f_out : k.x;
+  rc = gmres_solve(h, form, k.b, x, nrhs, tol, info, st);
+  if (rc != HPS_OK && rc != HPS_ENOCONV) return rc;
+  if (!fdev) {
+    HPS_CUDA_TRY(cudaMemcpyAsync(f_out, x, (size_t)nrhs * h->nf * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  }
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return rc;
+}
+
+long long hps_export(hps_handle* h, int what, int index, double* host_out) {
+  if (!h) {
+    set_error("hps_export: NULL handle");
+    return HPS_EINVAL;
+  }
+  if (cudaSetDevice(h->dev) != cudaSuccess) {
+    set_error("hps_export: cudaSetDevice failed");
+    return HPS_ECUDA;
+  }
+  cudaStreamSynchronize(h->stream);
+  const int q2 = h->q * h->q;
+  auto copy2d = [&](const void* src, size_t es, int rows, int cols, int ld, bool f32) -> long long {
+    const long long count = 2LL * rows * cols;
+    if (!host_out) return count;
+    if (!f32) {
+      if (cudaMemcpy2D(host_out, cols * sizeof(double2), src, (size_t)ld * es, cols * sizeof(double2), rows,
+                       cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("hps_export: copy failed");
+        return HPS_ECUDA;
+      }
+    } else {
+      std::vector<float2> tmp((size_t)rows * cols);
+      if (cudaMemcpy2D(tmp.data(), cols * sizeof(float2), src, (size_t)ld * es, cols * sizeof(float2), rows,
+                       cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("hps_export: copy failed");
+        return HPS_ECUDA;
+      }
+      for (size_t i = 0; i < tmp.size(); ++i) {
+        host_out[2 * i] = tmp[i].x;
+        host_out[2 * i + 1] = tmp[i].y;
+      }
+    }
+    return count;
+  };
+  switch (what) {
+    case HPS_EXPORT_R:
+      if (index < 0 || index >= h->nl) break;
+      return copy2d(h->R64 + (size_t)index * h->nb * h->ldR, sizeof(double2), h->nb, h->nb, h->ldR, false);
+    case HPS_EXPORT_H:
+      if (index < 0 || index >= h->nl) break;
+      return copy2d(h->H64 + (size_t)index * h->nb * h->ldH, sizeof(double2), h->nb, h->ni, h->ldH, false);
+    case HPS_EXPORT_LAMBDA:
+      if (index < 0 || index >= h->nl || !h->has_precond) break;
+      return copy2d(h->lambda + index, sizeof(double2), 1, 1, 1, false);
+    case HPS_EXPORT_KC: {
+      if (!h->has_precond || index < 0 || index >= h->ct.ncl) break;
+      const int nint = (h->ct.cl_slot_begin[index + 1] - h->ct.cl_slot_begin[index]) * q2;
+      const int ld = (int)rup4(nint);
+      if (h->Kc64) return copy2d(h->Kc64 + h->ct.cl_kc_off[index], sizeof(double2), nint, nint, ld, false);
+      return copy2d(h->Kc32 + h->ct.cl_kc_off[index], sizeof(float2), nint, nint, ld, true);
+    }
+    case HPS_EXPORT_B: {
+      if (!h->has_precond || index < 0 || index >= h->nl) break;
+      const int ni_ = __builtin_popcount(h->ct.int_mask[index]);
+      const int rows = ni_ * q2, cols = (6 - ni_) * q2, ld = (int)rup4(cols);
+      if (rows == 0) return 0;
+      if (h->B64) return copy2d(h->B64 + h->ct.b_off[index], sizeof(double2), rows, cols, ld, false);
+      return copy2d(h->B32 + h->ct.b_off[index], sizeof(float2), rows, cols, ld, true);
+    }
+    default:
+      break;
+  }
+  set_error("hps_export: bad 'what' or index");
+  return HPS_EINVAL;
+}
+
+size_t hps_memory_bytes(const hps_handle* h) { return h ? h->bytes + h->ks.bytes : 0; }
+
+int hps_destroy(hps_handle* h) {
+  free_handle(h);
+  return HPS_OK;
+}
+
+}  // extern "C"

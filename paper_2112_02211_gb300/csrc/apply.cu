@@ -1,0 +1,516 @@
+// Per-iteration operators of the HPS face system, as one family of
+// HBM-streaming batched GEMV kernels ("items" of q^2 matrix rows each):
+//
+//  * apply     y = f + Pi (R f)           (leaf ItI maps, Sec. 2.2, eq. (inter))
+//  * residual  y = b - (f + Pi (R f))
+//  * rhs       b = tbar - Pi (H s)        (body-load response of each leaf)
+//  * precond   z = J^{-1} r on 2x2x2 clusters (Sec. 4, Algorithm 4 in face form):
+//      stage B  z_ext = r_ext,  t = r_int - B r_ext   (B = internal rows of R~)
+//      stage K  z_int = K_c t                          (K_c = (I + D)^{-1})
+//
+// An item is (leaf, face) for apply/rhs/B (rows of that face's block) and a
+// cluster-internal slot for K.  The swap Pi is fused into the store: the rows
+// of leaf tau's face k produce the incoming data of the neighbour across k,
+// so every output slot has exactly one writer and no atomics are needed.
+// Faces on the boundary of the cube only copy (their rows of R are never
+// read).  A CTA stages the item's input vector in shared memory; each warp
+// streams RPW matrix rows with 16-byte loads (1 complex double or 2 complex
+// floats per lane per load), accumulates in the matrix's precision and
+// reduces with warp shuffles.
+#include <algorithm>
+
+#include "common.cuh"
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+template <class TM> struct MT;
+template <> struct MT<double2> {
+  static constexpr int VPL = 1;
+  using Acc = double2;
+  __device__ static __forceinline__ void load(const double2* p, double2 (&v)[1]) { v[0] = __ldg(p); }
+};
+template <> struct MT<float2> {
+  static constexpr int VPL = 2;
+  using Acc = float2;
+  __device__ static __forceinline__ void load(const float2* p, float2 (&v)[2]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
+  }
+};
+
+struct ItemInfo {
+  const void* mat;
+  long long xoff;  // base offset of the input vector (per rhs)
+  long long ooff;  // base offset of the output (per rhs)
+  long long aoff;  // auxiliary offset (neighbour input / residual base)
+  int ld, ncols;
+  int leaf, face, nbr;
+  int mask;        // precond B: internal-face mask of the leaf
+};
+
+// ---------------------------------------------------------------------------
+// Policies
+// ---------------------------------------------------------------------------
+template <class TM_, class TIN, class TOUT>
+struct ApplyP {
+  using TM = TM_;
+  using Acc = typename MT<TM>::Acc;
+  struct Args {
+    const TM* R;
+    int ldR, nb, q2;
+    GridDims g;
+    const TIN* f;
+    TOUT* y;
+    const double2* bvec;  // residual mode: y = b - (I + Pi R) f
+    long long nf;
+    int nrhs;
+    long long nitems;
+  };
+  __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
+    it.leaf = (int)(item / 6);
+    it.face = (int)(item % 6);
+    it.nbr = A.g.neighbor(it.leaf, it.face);
+    it.xoff = (long long)it.leaf * A.nb;
+    if (it.nbr < 0) {
+      it.ooff = it.xoff + (long long)it.face * A.q2;
+      return false;
+    }
+    it.mat = A.R + (long long)it.leaf * A.nb * A.ldR + (long long)it.face * A.q2 * A.ldR;
+    it.ld = A.ldR;
+    it.ncols = A.nb;
+    it.ooff = (long long)it.nbr * A.nb + (long long)(it.face ^ 1) * A.q2;
+    return true;
+  }
+  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
+    return cvt<Acc>(A.f[rhs * A.nf + it.xoff + c]);
+  }
+  __device__ static void finish(const Args& A, long long o, double2 g) {
+    double2 v = cadd(cvt<double2>(A.f[o]), g);
+    if (A.bvec) v = csub(A.bvec[o], v);
+    A.y[o] = cvt<TOUT>(v);
+  }
+  __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
+    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
+      const int rhs = idx / A.q2, j = idx % A.q2;
+      finish(A, rhs * A.nf + it.ooff + j, cvt<double2>(outs[idx]));
+    }
+  }
+  __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
+    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
+      const int rhs = idx / A.q2, j = idx % A.q2;
+      finish(A, rhs * A.nf + it.ooff + j, make_double2(0.0, 0.0));
+    }
+  }
+};
+
+struct RhsP {
+  using TM = double2;
+  using Acc = double2;
+  struct Args {
+    const double2* H;
+    int ldH, ni, nb, q2;
+    GridDims g;
+    const double2* s;
+    const double2* t;
+    double2* out;
+    long long nf, nint;
+    int nrhs;
+    long long nitems;
+  };
+  __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
+    it.leaf = (int)(item / 6);
+    it.face = (int)(item % 6);
+    it.nbr = A.g.neighbor(it.leaf, it.face);
+    if (it.nbr < 0) {
+      it.ooff = (long long)it.leaf * A.nb + (long long)it.face * A.q2;
+      return false;
+    }
+    it.ooff = (long long)it.nbr * A.nb + (long long)(it.face ^ 1) * A.q2;
+    if (!A.s) return false;
+    it.mat = A.H + (long long)it.leaf * A.nb * A.ldH + (long long)it.face * A.q2 * A.ldH;
+    it.ld = A.ldH;
+    it.ncols = A.ni;
+    it.xoff = (long long)it.leaf * A.ni;
+    return true;
+  }
+  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
+    return A.s[rhs * A.nint + it.xoff + c];
+  }
+  __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
+    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
+      const int rhs = idx / A.q2, j = idx % A.q2;
+      A.out[rhs * A.nf + it.ooff + j] = make_double2(-outs[idx].x, -outs[idx].y);
+    }
+  }
+  __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
+    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
+      const int rhs = idx / A.q2, j = idx % A.q2;
+      const long long o = rhs * A.nf + it.ooff + j;
+      A.out[o] = (it.nbr < 0 && A.t) ? A.t[o] : make_double2(0.0, 0.0);
+    }
+  }
+};
+
+template <class TM_, class TIN, class TOUT>
+struct PrecBP {
+  using TM = TM_;
+  using Acc = typename MT<TM>::Acc;
+  struct Args {
+    const TM* B;
+    const long long* b_off;
+    const uint8_t* int_mask;
+    const int* lf_slot;
+    int nb, q2;
+    GridDims g;
+    const TIN* r;
+    TOUT* z;
+    TOUT* t;
+    long long nf, tstride;
+    int nrhs;
+    long long nitems;
+  };
+  __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
+    it.leaf = (int)(item / 6);
+    it.face = (int)(item % 6);
+    const int mask = A.int_mask[it.leaf];
+    it.mask = mask;
+    it.xoff = (long long)it.leaf * A.nb;
+    if (!(mask & (1 << it.face))) {
+      it.ooff = it.xoff + (long long)it.face * A.q2;
+      return false;
+    }
+    const int rb = __popc(mask & ((1 << it.face) - 1));
+    const int next = 6 - __popc(mask);
+    it.ncols = next * A.q2;
+    it.ld = (int)rup4(it.ncols);
+    it.mat = A.B + A.b_off[it.leaf] + (long long)rb * A.q2 * it.ld;
+    it.nbr = A.g.neighbor(it.leaf, it.face);
+    it.aoff = (long long)it.nbr * A.nb + (long long)(it.face ^ 1) * A.q2;
+    it.ooff = (long long)A.lf_slot[it.nbr * 6 + (it.face ^ 1)] * A.q2;
+    return true;
+  }
+  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
+    int e = c / A.q2;
+    int f = 0;
+    for (; f < 6; ++f)
+      if (!(it.mask & (1 << f))) {
+        if (e == 0) break;
+        --e;
+      }
+    return cvt<Acc>(A.r[rhs * A.nf + it.xoff + (long long)f * A.q2 + c % A.q2]);
+  }
+  __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
+    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
+      const int rhs = idx / A.q2, j = idx % A.q2;
+      const double2 v = csub(cvt<double2>(A.r[rhs * A.nf + it.aoff + j]), cvt<double2>(outs[idx]));
+      A.t[rhs * A.tstride + it.ooff + j] = cvt<TOUT>(v);
+    }
+  }
+  __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
+    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
+      const int rhs = idx / A.q2, j = idx % A.q2;
+      const long long o = rhs * A.nf + it.ooff + j;
+      A.z[o] = cvt<TOUT>(cvt<double2>(A.r[o]));
+    }
+  }
+};
+
+template <class TM_, class TIN, class TOUT>
+struct PrecKP {
+  using TM = TM_;
+  using Acc = typename MT<TM>::Acc;
+  struct Args {
+    const TM* K;
+    const long long* kc_off;
+    const int* cl_slot_begin;
+    const int* slot_cluster;
+    const int* slot_lf;
+    int nb, q2;
+    const TIN* t;
+    TOUT* z;
+    long long nf, tstride;
+    int nrhs;
+    long long nitems;
+  };
+  __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
+    const int gs = (int)item;
+    const int c = A.slot_cluster[gs];
+    const int s0 = A.cl_slot_begin[c], ns = A.cl_slot_begin[c + 1] - s0;
+    it.ncols = ns * A.q2;
+    it.ld = (int)rup4(it.ncols);
+    it.mat = A.K + A.kc_off[c] + (long long)(gs - s0) * A.q2 * it.ld;
+    it.xoff = (long long)s0 * A.q2;
+    const int lf = A.slot_lf[gs];
+    it.ooff = (long long)(lf / 6) * A.nb + (long long)(lf % 6) * A.q2;
+    return true;
+  }
+  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
+    return cvt<Acc>(A.t[rhs * A.tstride + it.xoff + c]);
+  }
+  __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
+    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
+      const int rhs = idx / A.q2, j = idx % A.q2;
+      A.z[rhs * A.nf + it.ooff + j] = cvt<TOUT>(cvt<double2>(outs[idx]));
+    }
+  }
+  __device__ static void copy(const Args&, const ItemInfo&, int, int) {}
+};
+
+// ---------------------------------------------------------------------------
+// The kernel.
+// ---------------------------------------------------------------------------
+template <class P, int NR, int RPW>
+__global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Args A, int xcap) {
+  using TM = typename P::TM;
+  using Acc = typename P::Acc;
+  constexpr int VPL = MT<TM>::VPL;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Acc* xs = reinterpret_cast<Acc*>(smraw);
+  Acc* outs = xs + NR * xcap;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nr = A.nrhs < NR ? A.nrhs : NR;
+  const int q2 = A.q2;
+  for (long long item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    ItemInfo it;
+    if (!P::decode(A, item, it)) {
+      P::copy(A, it, nr, tid);
+      continue;
+    }
+    const int ncp = (it.ncols + VPL - 1) / VPL * VPL;
+    for (int idx = tid; idx < NR * ncp; idx += kThreads) {
+      const int rr = idx / ncp, c = idx % ncp;
+      xs[rr * ncp + c] = (rr < nr && c < it.ncols) ? P::load_x(A, it, rr, c) : czero<Acc>();
+    }
+    __syncthreads();
+    const TM* mat = reinterpret_cast<const TM*>(it.mat);
+    for (int r0 = warp * RPW; r0 < q2; r0 += kWarps * RPW) {
+      Acc acc[RPW][NR];
+#pragma unroll
+      for (int i = 0; i < RPW; ++i)
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) acc[i][rr] = czero<Acc>();
+#pragma unroll 2
+      for (int c = lane * VPL; c < ncp; c += 32 * VPL) {
+        TM mv[RPW][VPL];
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+          if (r0 + i < q2) {
+            MT<TM>::load(mat + (long long)(r0 + i) * it.ld + c, mv[i]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) mv[i][v] = czero<TM>();
+          }
+        }
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) {
+            const Acc xv = xs[rr * ncp + c + v];
+#pragma unroll
+            for (int i = 0; i < RPW; ++i) cfma(acc[i][rr], mv[i][v], xv);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RPW; ++i)
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+          acc[i][rr].x = warp_sum(acc[i][rr].x);
+          acc[i][rr].y = warp_sum(acc[i][rr].y);
+        }
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < RPW; ++i)
+          if (r0 + i < q2)
+#pragma unroll
+            for (int rr = 0; rr < NR; ++rr) outs[rr * q2 + r0 + i] = acc[i][rr];
+      }
+    }
+    __syncthreads();
+    P::store(A, it, outs, nr, tid);
+    __syncthreads();
+  }
+}
+
+template <class P, int NR, int RPW>
+cudaError_t launch_one(const typename P::Args& A, int xcap, int q2, int nsm, cudaStream_t st) {
+  using Acc = typename P::Acc;
+  const size_t smem = ((size_t)NR * xcap + (size_t)NR * q2) * sizeof(Acc);
+  auto kern = seg_gemv_kernel<P, NR, RPW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  occ = std::max(occ, 1);
+  long long grid = std::min<long long>(A.nitems, (long long)nsm * occ);
+  if (grid <= 0) return cudaSuccess;
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(A, xcap);
+  return cudaGetLastError();
+}
+
+// Launch over right-hand-side groups of at most 8 (each group re-reads the matrix).
+template <class P, class Shift>
+cudaError_t launch_groups(typename P::Args A, int nrhs, int xcap, int q2, int nsm, cudaStream_t st, Shift shift) {
+  for (int r0 = 0; r0 < nrhs; r0 += 8) {
+    typename P::Args B = A;
+    const int nr = std::min(8, nrhs - r0);
+    shift(B, r0);
+    B.nrhs = nr;
+    cudaError_t e;
+    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, q2, nsm, st);
+    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, q2, nsm, st);
+    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, q2, nsm, st);
+    else e = launch_one<P, 8, 1>(B, xcap, q2, nsm, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int xcap_of(const hps_handle* h) {
+  int mx = std::max(h->nb, h->ni);
+  if (h->has_precond)
+    for (int c = 0; c < h->ct.ncl; ++c)
+      mx = std::max(mx, (h->ct.cl_slot_begin[c + 1] - h->ct.cl_slot_begin[c]) * h->q * h->q);
+  return (int)round_up(mx, 64);
+}
+
+template <class TM, class TIN, class TOUT>
+cudaError_t apply_t(const hps_handle* h, const TM* R, const TIN* f, TOUT* y, const double2* bvec, int nrhs,
+                    cudaStream_t st) {
+  using P = ApplyP<TM, TIN, TOUT>;
+  typename P::Args A;
+  A.R = R;
+  A.ldR = h->ldR;
+  A.nb = h->nb;
+  A.q2 = h->q * h->q;
+  A.g = GridDims{h->nx, h->ny, h->nz};
+  A.f = f;
+  A.y = y;
+  A.bvec = bvec;
+  A.nf = h->nf;
+  A.nrhs = nrhs;
+  A.nitems = (long long)h->nl * 6;
+  return launch_groups<P>(A, nrhs, xcap_of(h), A.q2, h->nsm, st, [&](typename P::Args& B, int r0) {
+    B.f += (long long)r0 * h->nf;
+    B.y += (long long)r0 * h->nf;
+    if (B.bvec) B.bvec += (long long)r0 * h->nf;
+  });
+}
+
+template <class TM, class TIN, class TOUT>
+cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* r, TOUT* z, TOUT* t, int nrhs,
+                      cudaStream_t st) {
+  const int q2 = h->q * h->q;
+  const long long tstride = (long long)h->ct.nslots * q2;
+  {
+    using P = PrecBP<TM, TIN, TOUT>;
+    typename P::Args A;
+    A.B = B;
+    A.b_off = h->dct.b_off;
+    A.int_mask = h->dct.int_mask;
+    A.lf_slot = h->dct.lf_slot;
+    A.nb = h->nb;
+    A.q2 = q2;
+    A.g = GridDims{h->nx, h->ny, h->nz};
+    A.r = r;
+    A.z = z;
+    A.t = t;
+    A.nf = h->nf;
+    A.tstride = tstride;
+    A.nrhs = nrhs;
+    A.nitems = (long long)h->nl * 6;
+    cudaError_t e = launch_groups<P>(A, nrhs, xcap_of(h), q2, h->nsm, st, [&](typename P::Args& X, int r0) {
+      X.r += (long long)r0 * h->nf;
+      X.z += (long long)r0 * h->nf;
+      X.t += (long long)r0 * tstride;
+    });
+    if (e != cudaSuccess) return e;
+  }
+  if (h->ct.nslots == 0) return cudaSuccess;
+  {
+    using P = PrecKP<TM, TOUT, TOUT>;
+    typename P::Args A;
+    A.K = K;
+    A.kc_off = h->dct.cl_kc_off;
+    A.cl_slot_begin = h->dct.cl_slot_begin;
+    A.slot_cluster = h->dct.slot_cluster;
+    A.slot_lf = h->dct.slot_lf;
+    A.nb = h->nb;
+    A.q2 = q2;
+    A.t = t;
+    A.z = z;
+    A.nf = h->nf;
+    A.tstride = tstride;
+    A.nrhs = nrhs;
+    A.nitems = h->ct.nslots;
+    return launch_groups<P>(A, nrhs, xcap_of(h), q2, h->nsm, st, [&](typename P::Args& X, int r0) {
+      X.t += (long long)r0 * tstride;
+      X.z += (long long)r0 * h->nf;
+    });
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const void* f, VType tout, void* y,
+                         const double2* bvec, int nrhs, bool residual, cudaStream_t st) {
+  if (!residual) bvec = nullptr;
+  if (!fp32_matrix) {
+    if (tin == VType::C128 && tout == VType::C128)
+      return apply_t(h, h->R64, (const double2*)f, (double2*)y, bvec, nrhs, st);
+    return cudaErrorInvalidValue;
+  }
+  if (tin == VType::C64 && tout == VType::C64)
+    return apply_t(h, h->R32, (const float2*)f, (float2*)y, bvec, nrhs, st);
+  if (tin == VType::C64 && tout == VType::C128)
+    return apply_t(h, h->R32, (const float2*)f, (double2*)y, bvec, nrhs, st);
+  if (tin == VType::C128 && tout == VType::C128)
+    return apply_t(h, h->R32, (const double2*)f, (double2*)y, bvec, nrhs, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
+                       cudaStream_t st) {
+  typename RhsP::Args A;
+  A.H = h->H64;
+  A.ldH = h->ldH;
+  A.ni = h->ni;
+  A.nb = h->nb;
+  A.q2 = h->q * h->q;
+  A.g = GridDims{h->nx, h->ny, h->nz};
+  A.s = s;
+  A.t = t;
+  A.out = b;
+  A.nf = h->nf;
+  A.nint = h->nint;
+  A.nrhs = nrhs;
+  A.nitems = (long long)h->nl * 6;
+  return launch_groups<RhsP>(A, nrhs, xcap_of(h), A.q2, h->nsm, st, [&](typename RhsP::Args& B, int r0) {
+    if (B.s) B.s += (long long)r0 * h->nint;
+    if (B.t) B.t += (long long)r0 * h->nf;
+    B.out += (long long)r0 * h->nf;
+  });
+}
+
+cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, const void* r, VType tout, void* z,
+                           void* scratch, int nrhs, cudaStream_t st) {
+  if (!fp32_matrix) {
+    if (tin == VType::C128 && tout == VType::C128)
+      return precond_t(h, h->B64, h->Kc64, (const double2*)r, (double2*)z, (double2*)scratch, nrhs, st);
+    return cudaErrorInvalidValue;
+  }
+  if (tout != VType::C64) return cudaErrorInvalidValue;
+  if (tin == VType::C64)
+    return precond_t(h, h->B32, h->Kc32, (const float2*)r, (float2*)z, (float2*)scratch, nrhs, st);
+  return precond_t(h, h->B32, h->Kc32, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st);
+}
+
+}  // namespace hps

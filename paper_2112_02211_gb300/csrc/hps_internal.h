@@ -1,0 +1,165 @@
+// Internal declarations of the HPS library: the handle and the kernel
+// launchers implemented in setup.cu, apply.cu and krylov.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hps.h"
+
+namespace hps {
+
+void set_error(const std::string& msg);
+
+// Throws-free error plumbing: every launcher returns cudaError_t and the API
+// layer converts it to HPS_ECUDA with the message.
+#define HPS_CUDA_TRY(expr)                                                          \
+  do {                                                                              \
+    cudaError_t e__ = (expr);                                                       \
+    if (e__ != cudaSuccess) {                                                       \
+      ::hps::set_error(std::string(#expr) + ": " + cudaGetErrorString(e__));        \
+      return HPS_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+inline long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// Offsets (in doubles) of the 1D tables in Handle::tables.
+struct TableLayout {
+  int p, q;
+  int x, D, D2, xg, wg, Q, Qi, total;
+  explicit TableLayout(int p_ = 4) : p(p_), q(p_ - 2) {
+    x = 0;
+    D = x + p;            // 3 axes, p*p each, scaled by 2/h_axis
+    D2 = D + 3 * p * p;   // squares of D
+    xg = D2 + 3 * p * p;  // Gauss nodes on [-1, 1]
+    wg = xg + q;          // Gauss weights
+    Q = wg + q;           // q x q: Chebyshev-interior -> Gauss interpolation
+    Qi = Q + q * q;       // inverse of Q
+    total = Qi + q * q;
+  }
+};
+
+// Cluster (block-Jacobi) bookkeeping, built on the host from integer grid
+// arithmetic and uploaded once.
+struct ClusterTables {
+  int ncl = 0;                       // clusters
+  int nslots = 0;                    // internal face slots over all clusters
+  std::vector<int> cl_leaf_begin;    // [ncl+1] into cl_leaves
+  std::vector<int> cl_leaves;        // leaves of each cluster, lexicographic
+  std::vector<int> cl_slot_begin;    // [ncl+1] first global slot of each cluster
+  std::vector<long long> cl_kc_off;  // [ncl] element offset of K_c (ld = kc_ld(c))
+  std::vector<int> slot_lf;          // [nslots] leaf*6+face of each slot
+  std::vector<int> slot_cluster;     // [nslots]
+  std::vector<int> lf_slot;          // [nleaves*6] slot of (leaf, face) or -1 if external
+  std::vector<uint8_t> int_mask;     // [nleaves] bit f: face f is internal to the leaf's cluster
+  std::vector<long long> b_off;      // [nleaves] element offset of B^leaf
+  long long kc_elems = 0, b_elems = 0;
+};
+
+struct DeviceClusterTables {
+  int* slot_lf = nullptr;
+  int* slot_cluster = nullptr;
+  int* cl_slot_begin = nullptr;
+  long long* cl_kc_off = nullptr;
+  int* lf_slot = nullptr;
+  uint8_t* int_mask = nullptr;
+  long long* b_off = nullptr;
+};
+
+struct KrylovSpace {
+  int m = 0, nrhs = 0, nblk = 0;
+  long long nf = 0;
+  double2* V = nullptr;      // (m+1) x nrhs x nf
+  double2* x = nullptr;      // nrhs x nf
+  double2* r = nullptr;      // nrhs x nf
+  double2* b = nullptr;      // nrhs x nf
+  double2* u = nullptr;      // nrhs x nf (V y)
+  void* z = nullptr;         // nrhs x nf, inner precision
+  void* zt = nullptr;        // precond scratch (internal slots), inner precision
+  double2* part = nullptr;   // nrhs x nblk x (m+1) partial dots
+  double2* hcol = nullptr;   // nrhs x (m+2) current Hessenberg column
+  double2* H = nullptr;      // nrhs x (m+1) x m, rotated
+  double* cs = nullptr;      // nrhs x m
+  double2* sn = nullptr;     // nrhs x m
+  double2* g = nullptr;      // nrhs x (m+1)
+  double2* y = nullptr;      // nrhs x m
+  double* est = nullptr;     // nrhs: |g_{j+1}| after the last step
+  double* nrm = nullptr;     // nrhs: norms
+  int* active = nullptr;     // nrhs
+  int* status = nullptr;     // device status word (breakdown etc.)
+  double2* s_dev = nullptr;  // staging for host inputs
+  double2* t_dev = nullptr;
+  double2* f_dev = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace hps
+
+struct hps_handle {
+  int dev = 0;
+  int nx = 0, ny = 0, nz = 0, p = 0, q = 0, n1 = 0, ni = 0, nb = 0, n = 0, nl = 0;
+  long long nf = 0, nint = 0;
+  double kappa = 0, eta = 0, h[3] = {0, 0, 0};
+  hps_options opt{};
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+
+  double* tables = nullptr;
+  hps::TableLayout tl;
+
+  // exact leaf maps (Gauss basis)
+  int ldR = 0, ldH = 0;
+  double2* R64 = nullptr;  // nl x nb x ldR
+  float2* R32 = nullptr;   // nl x nb x ldR
+  double2* H64 = nullptr;  // nl x nb x ldH
+  double2* lambda = nullptr;  // nl
+
+  // preconditioner
+  bool has_precond = false;
+  hps::ClusterTables ct;
+  hps::DeviceClusterTables dct;
+  double2* Kc64 = nullptr;
+  float2* Kc32 = nullptr;
+  double2* B64 = nullptr;
+  float2* B32 = nullptr;
+  void* pc_scratch = nullptr;  // nslots*q^2*max_rhs complex double (precond t buffer)
+
+  hps::KrylovSpace ks;
+  size_t bytes = 0;
+};
+
+namespace hps {
+
+// ---- setup.cu ----
+cudaError_t launch_tables(double* tables, const TableLayout& tl, double hx, double hy, double hz,
+                          cudaStream_t st);
+cudaError_t launch_nodes(const double* tables, const TableLayout& tl, int nx, int ny, int nz,
+                         double* interior_xyz_dev, double* face_xyz_dev, cudaStream_t st);
+// Builds R (and H) for all leaves; see setup.cu.
+int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st);
+int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st);
+void build_cluster_tables(hps_handle* h, int width);
+
+// ---- apply.cu ----
+enum class VType { C128, C64 };
+// y = (I + Pi R) f  (mode 0) or y = b - (I + Pi R) f (mode 1), R in FP64 or FP32.
+cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const void* f,
+                         VType tout, void* y, const double2* bvec, int nrhs, bool residual,
+                         cudaStream_t st);
+cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
+                       cudaStream_t st);
+cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, const void* r,
+                           VType tout, void* z, void* scratch, int nrhs, cudaStream_t st);
+
+// ---- krylov.cu ----
+int krylov_alloc(hps_handle* h, int nrhs);
+void krylov_free(hps_handle* h);
+int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol,
+                hps_solve_info* info, cudaStream_t st);
+
+}  // namespace hps

@@ -1,0 +1,604 @@
+// Restarted GMRES (Saad and Schultz 1986; PETSc KSP GMRES in the paper,
+// Sec. 5.2) on the face system, right-preconditioned by the cluster
+// block-Jacobi operator, with every Krylov step on the device in FP64:
+//
+//   z = M^{-1} v_j            (FP64 form: complex FP64; mixed form: complex FP32)
+//   w = A z                   (same precision as z, written as FP64)
+//   h = V^H w, w -= V h       (classical Gram-Schmidt, applied twice: CGS2)
+//   h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
+//   Givens rotation of the Hessenberg column, residual estimate |g_{j+1}|.
+//
+// At the end of each cycle x += M^{-1} (V y) and the true residual
+// b - A x is recomputed with the FP64 leaf maps.  In the mixed form that
+// restart residual is what restores FP64 accuracy: each cycle solves the
+// correction equation with the FP32 operator and the FP64 residual drives the
+// next cycle (iterative refinement with a GMRES inner solver).
+//
+// Dot products are formed as fixed-order block partials (2048 entries per
+// block, warp shuffles, then a sequential sum over blocks), so results are
+// bitwise reproducible run to run.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+constexpr int kT = 256;      // threads per block
+constexpr int kE = 8;        // elements per thread
+constexpr int kChunk = kT * kE;
+constexpr int kG = 8;        // vectors per register group
+
+__device__ __forceinline__ void block_reduce_store(double2 (&acc)[kG], int ng, double2* out) {
+  __shared__ double2 red[kT / 32][kG];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < kG; ++g) {
+    acc[g].x = warp_sum(acc[g].x);
+    acc[g].y = warp_sum(acc[g].y);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int g = 0; g < kG; ++g) red[warp][g] = acc[g];
+  __syncthreads();
+  if (threadIdx.x < ng) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int w = 0; w < kT / 32; ++w) s = cadd(s, red[w][threadIdx.x]);
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+struct VecArgs {
+  const double2* V;  // basis: vector j of rhs r at V + (j*nrhs + r)*nf
+  double2* w;        // rhs r at w + r*nf
+  long long nf;
+  int nrhs, nvec, M1, nblk;
+  double2* part;     // [rhs][nblk][M1]
+  const double2* coef;  // [rhs][cstride]
+  int cstride;
+  const int* active;
+};
+
+// part = block partials of V_{0..nvec-1}^H w
+__global__ void __launch_bounds__(kT) mdot_kernel(VecArgs a) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (a.active && !a.active[rhs]) return;
+  const long long base = (long long)blk * kChunk + threadIdx.x;
+  const double2* w = a.w + rhs * a.nf;
+  double2 wv[kE];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const long long i = base + (long long)e * kT;
+    wv[e] = (i < a.nf) ? w[i] : make_double2(0.0, 0.0);
+  }
+  double2* out = a.part + ((long long)rhs * a.nblk + blk) * a.M1;
+  for (int g0 = 0; g0 < a.nvec; g0 += kG) {
+    const int ng = min(kG, a.nvec - g0);
+    double2 acc[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) acc[g] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      if (g < ng) {
+        const double2* v = a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf;
+#pragma unroll
+        for (int e = 0; e < kE; ++e) {
+          const long long i = base + (long long)e * kT;
+          if (i < a.nf) {
+            const double2 vv = v[i];
+            acc[g].x += vv.x * wv[e].x + vv.y * wv[e].y;
+            acc[g].y += vv.x * wv[e].y - vv.y * wv[e].x;
+          }
+        }
+      }
+    }
+    block_reduce_store(acc, ng, out + g0);
+  }
+}
+
+// w -= V coef; then (mode 1) partial dots V^H w, or (mode 2) partial ||w||^2.
+__global__ void __launch_bounds__(kT) axpy_kernel(VecArgs a, int mode) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (a.active && !a.active[rhs]) return;
+  __shared__ double2 cf[64];
+  for (int j = threadIdx.x; j < a.nvec; j += kT) cf[j] = a.coef[(long long)rhs * a.cstride + j];
+  __syncthreads();
+  const long long base = (long long)blk * kChunk + threadIdx.x;
+  double2* w = a.w + rhs * a.nf;
+  double2 wv[kE];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const long long i = base + (long long)e * kT;
+    wv[e] = (i < a.nf) ? w[i] : make_double2(0.0, 0.0);
+  }
+  for (int j = 0; j < a.nvec; ++j) {
+    const double2* v = a.V + ((long long)j * a.nrhs + rhs) * a.nf;
+    const double2 c = cf[j];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      const long long i = base + (long long)e * kT;
+      if (i < a.nf) {
+        const double2 vv = v[i];
+        wv[e].x -= c.x * vv.x - c.y * vv.y;
+        wv[e].y -= c.x * vv.y + c.y * vv.x;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const long long i = base + (long long)e * kT;
+    if (i < a.nf) w[i] = wv[e];
+  }
+  double2* out = a.part + ((long long)rhs * a.nblk + blk) * a.M1;
+  if (mode == 1) {
+    for (int g0 = 0; g0 < a.nvec; g0 += kG) {
+      const int ng = min(kG, a.nvec - g0);
+      double2 acc[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) acc[g] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        if (g < ng) {
+          const double2* v = a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf;
+#pragma unroll
+          for (int e = 0; e < kE; ++e) {
+            const long long i = base + (long long)e * kT;
+            if (i < a.nf) {
+              const double2 vv = v[i];
+              acc[g].x += vv.x * wv[e].x + vv.y * wv[e].y;
+              acc[g].y += vv.x * wv[e].y - vv.y * wv[e].x;
+            }
+          }
+        }
+      }
+      block_reduce_store(acc, ng, out + g0);
+    }
+  } else if (mode == 2) {
+    double2 acc[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) acc[g] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int e = 0; e < kE; ++e) acc[0].x += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
+    block_reduce_store(acc, 1, out);
+  }
+}
+
+// out[rhs][i] (=|+=) sum over blocks of part[rhs][blk][i], in block order.
+__global__ void reduce_kernel(const double2* part, int nblk, int nvec, int M1, double2* out, int ostride,
+                              int accumulate, const int* active) {
+  const int rhs = blockIdx.x;
+  if (active && !active[rhs]) return;
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    const double2* p = part + (long long)rhs * nblk * M1 + i;
+    for (int b = 0; b < nblk; ++b) s = cadd(s, p[(long long)b * M1]);
+    double2* o = out + (long long)rhs * ostride + i;
+    *o = accumulate ? cadd(*o, s) : s;
+  }
+}
+
+struct GivensArgs {
+  int nrhs, m, j, M1, nblk;
+  const double2* part;  // norm^2 partials in slot 0
+  double2* hcol;        // [rhs][M1+1]: h1 (CGS pass 1)
+  const double2* h2;    // [rhs][M1]: CGS pass 2
+  double2* H;           // [rhs][M1][m]
+  double* cs;           // [rhs][m]
+  double2* sn;          // [rhs][m]
+  double2* g;           // [rhs][M1]
+  double* est;          // [rhs]
+  double* invn;         // [rhs]
+  int* active;          // [rhs]
+  int* kcount;          // [rhs]
+  const double* target; // [rhs]
+  int* any_active;
+};
+
+// One thread per right-hand side: finish column j of the Hessenberg matrix,
+// apply the previous rotations, make the new one, update g.
+__global__ void givens_kernel(GivensArgs a) {
+  const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= a.nrhs) return;
+  if (!a.active[rhs]) return;
+  const int j = a.j;
+  double nrm2 = 0.0;
+  for (int b = 0; b < a.nblk; ++b) nrm2 += a.part[((long long)rhs * a.nblk + b) * a.M1].x;
+  const double hn = sqrt(nrm2);
+  double2* Hc = a.H + (long long)rhs * a.M1 * a.m;  // Hc[i*m + j]
+  for (int i = 0; i <= j; ++i) Hc[i * a.m + j] = cadd(a.hcol[(long long)rhs * (a.M1 + 1) + i], a.h2[(long long)rhs * a.M1 + i]);
+  Hc[(j + 1) * a.m + j] = make_double2(hn, 0.0);
+  double* cs = a.cs + (long long)rhs * a.m;
+  double2* sn = a.sn + (long long)rhs * a.m;
+  for (int i = 0; i < j; ++i) {
+    const double2 x = Hc[i * a.m + j], y = Hc[(i + 1) * a.m + j];
+    Hc[i * a.m + j] = cadd(cscale(x, cs[i]), cmul(sn[i], y));
+    const double2 sc = make_double2(sn[i].x, -sn[i].y);
+    Hc[(i + 1) * a.m + j] = csub(cscale(y, cs[i]), cmul(sc, x));
+  }
+  const double2 x = Hc[j * a.m + j], y = Hc[(j + 1) * a.m + j];
+  const double ax = sqrt(cabs2(x)), den = sqrt(cabs2(x) + cabs2(y));
+  double c;
+  double2 s;
+  if (ax == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+  } else {
+    c = ax / den;
+    const double2 ph = cscale(x, 1.0 / ax);
+    s = cscale(cmul(ph, make_double2(y.x, -y.y)), 1.0 / den);
+  }
+  cs[j] = c;
+  sn[j] = s;
+  Hc[j * a.m + j] = cadd(cscale(x, c), cmul(s, y));
+  Hc[(j + 1) * a.m + j] = make_double2(0.0, 0.0);
+  double2* g = a.g + (long long)rhs * a.M1;
+  const double2 gj = g[j];
+  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
+  g[j] = cscale(gj, c);
+  const double e = sqrt(cabs2(g[j + 1]));
+  a.est[rhs] = e;
+  a.kcount[rhs] = j + 1;
+  const bool breakdown = !(hn > 1e-300 * fmax(1.0, den));
+  a.invn[rhs] = breakdown ? 0.0 : 1.0 / hn;
+  if (breakdown || e <= a.target[rhs] || j + 1 >= a.m) {
+    a.active[rhs] = 0;
+  } else {
+    atomicOr(a.any_active, 1);
+  }
+}
+
+// w <- w * invn[rhs]
+__global__ void scale_kernel(double2* w, long long nf, int nrhs, const double* invn, const int* active) {
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  const double s = invn[rhs];
+  double2* p = w + rhs * nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x)
+    p[i] = cscale(p[i], s);
+}
+
+// dst = src * invn[rhs]
+__global__ void scale_copy_kernel(const double2* src, double2* dst, long long nf, const double* invn) {
+  const int rhs = blockIdx.y;
+  const double s = invn[rhs];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x)
+    dst[rhs * nf + i] = cscale(src[rhs * nf + i], s);
+}
+
+// y = H(0:k,0:k)^{-1} g(0:k) per rhs (upper triangular after the rotations).
+__global__ void lsq_kernel(int nrhs, int m, int M1, const double2* H, const double2* g, const int* kcount, double2* y) {
+  const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= nrhs) return;
+  const int k = kcount[rhs];
+  const double2* Hc = H + (long long)rhs * M1 * m;
+  double2* yr = y + (long long)rhs * m;
+  for (int i = 0; i < m; ++i) yr[i] = make_double2(0.0, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[(long long)rhs * M1 + i];
+    for (int l = i + 1; l < k; ++l) s = csub(s, cmul(Hc[i * m + l], yr[l]));
+    const double2 d = Hc[i * m + i];
+    yr[i] = (d.x == 0.0 && d.y == 0.0) ? make_double2(0.0, 0.0) : cmul(s, cinv(d));
+  }
+}
+
+// u = sum_{j<kmax} y_j v_j
+__global__ void combine_kernel(const double2* V, int nrhs, long long nf, int kmax, int m, const double2* y, double2* u) {
+  const int rhs = blockIdx.y;
+  __shared__ double2 ys[64];
+  for (int j = threadIdx.x; j < kmax; j += blockDim.x) ys[j] = y[(long long)rhs * m + j];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int j = 0; j < kmax; ++j) {
+      const double2 v = V[((long long)j * nrhs + rhs) * nf + i];
+      cfma(s, ys[j], v);
+    }
+    u[rhs * nf + i] = s;
+  }
+}
+
+template <class T>
+__global__ void xpy_kernel(double2* x, const T* z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = cadd(x[i], cvt<double2>(z[i]));
+}
+
+__global__ void cast_vec_kernel(const double2* in, float2* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = cvt<float2>(in[i]);
+}
+
+// norms[rhs] = ||x_rhs||_2 from block partials
+__global__ void norm_partial_kernel(const double2* x, long long nf, int nblk, double* part) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  double s = 0.0;
+  for (long long i = (long long)blk * blockDim.x + threadIdx.x; i < nf; i += (long long)nblk * blockDim.x) {
+    const double2 v = x[rhs * nf + i];
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = warp_sum(s);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[(long long)rhs * nblk + blk] = t;
+  }
+}
+
+__global__ void norm_final_kernel(const double* part, int nblk, int nrhs, double* out) {
+  const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= nrhs) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(long long)rhs * nblk + b];
+  out[rhs] = sqrt(s);
+}
+
+struct Flt {};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int krylov_alloc(hps_handle* h, int nrhs) {
+  KrylovSpace& k = h->ks;
+  const int m = h->opt.restart;
+  if (k.V && k.nrhs >= nrhs && k.m == m) return HPS_OK;
+  krylov_free(h);
+  k.m = m;
+  k.nrhs = nrhs;
+  k.nf = h->nf;
+  k.nblk = (int)((h->nf + kChunk - 1) / kChunk);
+  const int M1 = m + 1;
+  const long long nf = h->nf;
+  size_t total = 0;
+  auto alloc = [&](void** p, size_t bytes) -> int {
+    bytes = std::max<size_t>(bytes, 16);
+    if (h->opt.hbm_budget && h->bytes + total + bytes > h->opt.hbm_budget) {
+      set_error("Krylov workspace exceeds the HBM budget");
+      return HPS_ENOMEM;
+    }
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc failed for the Krylov workspace");
+      return HPS_ENOMEM;
+    }
+    total += bytes;
+    return HPS_OK;
+  };
+  int rc;
+  const size_t vb = (size_t)nrhs * nf * sizeof(double2);
+  if ((rc = alloc((void**)&k.V, vb * M1))) return rc;
+  if ((rc = alloc((void**)&k.x, vb))) return rc;
+  if ((rc = alloc((void**)&k.r, vb))) return rc;
+  if ((rc = alloc((void**)&k.b, vb))) return rc;
+  if ((rc = alloc((void**)&k.u, vb))) return rc;
+  if ((rc = alloc(&k.z, vb))) return rc;
+  const size_t ts = std::max<size_t>(1, (size_t)h->ct.nslots * h->q * h->q) * nrhs * sizeof(double2);
+  if ((rc = alloc(&k.zt, ts))) return rc;
+  if ((rc = alloc((void**)&k.part, (size_t)nrhs * k.nblk * M1 * sizeof(double2)))) return rc;
+  if ((rc = alloc((void**)&k.hcol, (size_t)nrhs * (M1 + 1) * sizeof(double2)))) return rc;
+  if ((rc = alloc((void**)&k.y, (size_t)nrhs * M1 * sizeof(double2)))) return rc;  // also h2
+  if ((rc = alloc((void**)&k.H, (size_t)nrhs * M1 * m * sizeof(double2)))) return rc;
+  if ((rc = alloc((void**)&k.cs, (size_t)nrhs * m * sizeof(double)))) return rc;
+  if ((rc = alloc((void**)&k.sn, (size_t)nrhs * m * sizeof(double2)))) return rc;
+  if ((rc = alloc((void**)&k.g, (size_t)nrhs * M1 * sizeof(double2)))) return rc;
+  if ((rc = alloc((void**)&k.est, (size_t)nrhs * 4 * sizeof(double)))) return rc;  // est, invn, target, norms
+  if ((rc = alloc((void**)&k.nrm, (size_t)nrhs * std::max(256, k.nblk) * sizeof(double)))) return rc;
+  if ((rc = alloc((void**)&k.active, (size_t)(2 * nrhs + 2) * sizeof(int)))) return rc;  // active, kcount, any, status
+  k.status = k.active + 2 * nrhs + 1;
+  k.bytes = total;
+  return HPS_OK;
+}
+
+void krylov_free(hps_handle* h) {
+  KrylovSpace& k = h->ks;
+  void* ptrs[] = {k.V, k.x, k.r, k.b, k.u, k.z, k.zt, k.part, k.hcol, k.y, k.H, k.cs, k.sn, k.g, k.est, k.nrm, k.active,
+                  k.s_dev, k.t_dev, k.f_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  k = KrylovSpace();
+}
+
+namespace {
+
+int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& out, cudaStream_t st) {
+  KrylovSpace& k = h->ks;
+  const int nblk = 256;
+  double* part = k.nrm;
+  double* res = k.est + 3 * k.nrhs;
+  norm_partial_kernel<<<dim3(nblk, nrhs), 256, 0, st>>>(x, h->nf, nblk, part);
+  HPS_CUDA_TRY(cudaGetLastError());
+  norm_final_kernel<<<(nrhs + 63) / 64, 64, 0, st>>>(part, nblk, nrhs, res);
+  HPS_CUDA_TRY(cudaGetLastError());
+  out.resize(nrhs);
+  HPS_CUDA_TRY(cudaMemcpyAsync(out.data(), res, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  return HPS_OK;
+}
+
+}  // namespace
+
+int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol, hps_solve_info* info,
+                cudaStream_t st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const bool mixed = (form == HPS_FORM_MIXED);
+  int rc = krylov_alloc(h, nrhs);
+  if (rc) return rc;
+  KrylovSpace& k = h->ks;
+  const int m = k.m, M1 = m + 1;
+  const long long nf = h->nf;
+  const size_t vb = (size_t)nrhs * nf * sizeof(double2);
+  double* est = k.est;
+  double* invn = k.est + nrhs;
+  double* target = k.est + 2 * nrhs;
+  int* active = k.active;
+  int* kcount = k.active + nrhs;
+  int* any_active = k.active + 2 * nrhs;
+  double2* h2 = k.y;  // pass-2 coefficients reuse the y buffer until the cycle ends
+  const int gblk = std::min<long long>(4 * h->nsm, (nf + 255) / 256);
+  const dim3 vgrid(gblk, nrhs);
+
+  std::vector<double> bnorm, rnorm;
+  if ((rc = vec_norms(h, b, nrhs, bnorm, st))) return rc;
+  HPS_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
+  HPS_CUDA_TRY(cudaMemcpyAsync(k.r, b, vb, cudaMemcpyDeviceToDevice, st));
+  rnorm = bnorm;
+  int its = 0, cycles = 0;
+  const double eps_inner = mixed ? 1e-6 : 0.0;
+  std::vector<double> htarget(nrhs), hinv(nrhs);
+  std::vector<int> hact(nrhs);
+  bool converged = false;
+  const bool pc = h->has_precond;
+  while (true) {
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r)
+      if (bnorm[r] > 0.0 && rnorm[r] > tol * bnorm[r]) all = false;
+    if (all) {
+      converged = true;
+      break;
+    }
+    if (its >= h->opt.maxit) break;
+    for (int r = 0; r < nrhs; ++r) {
+      const bool act = bnorm[r] > 0.0 && rnorm[r] > tol * bnorm[r];
+      hact[r] = act ? 1 : 0;
+      htarget[r] = std::max(0.5 * tol * bnorm[r], eps_inner * rnorm[r]);
+      hinv[r] = act ? 1.0 / rnorm[r] : 0.0;
+    }
+    HPS_CUDA_TRY(cudaMemcpyAsync(active, hact.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    HPS_CUDA_TRY(cudaMemcpyAsync(target, htarget.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    HPS_CUDA_TRY(cudaMemcpyAsync(invn, hinv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    HPS_CUDA_TRY(cudaMemsetAsync(kcount, 0, nrhs * sizeof(int), st));
+    HPS_CUDA_TRY(cudaMemsetAsync(k.g, 0, (size_t)nrhs * M1 * sizeof(double2), st));
+    {
+      std::vector<double2> g0(nrhs);
+      for (int r = 0; r < nrhs; ++r) g0[r] = make_double2(hact[r] ? rnorm[r] : 0.0, 0.0);
+      for (int r = 0; r < nrhs; ++r)
+        HPS_CUDA_TRY(cudaMemcpyAsync(k.g + (long long)r * M1, &g0[r], sizeof(double2), cudaMemcpyHostToDevice, st));
+      HPS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    scale_copy_kernel<<<vgrid, 256, 0, st>>>(k.r, k.V, nf, invn);
+    HPS_CUDA_TRY(cudaGetLastError());
+    int jdone = 0;
+    for (int j = 0; j < m && its < h->opt.maxit; ++j) {
+      double2* vj = k.V + (long long)j * nrhs * nf;
+      double2* w = k.V + (long long)(j + 1) * nrhs * nf;
+      // z = M^{-1} v_j ; w = A z
+      if (mixed) {
+        if (pc) {
+          HPS_CUDA_TRY(launch_precond(h, true, VType::C128, vj, VType::C64, k.z, k.zt, nrhs, st));
+          HPS_CUDA_TRY(launch_apply(h, true, VType::C64, k.z, VType::C128, w, nullptr, nrhs, false, st));
+        } else {
+          HPS_CUDA_TRY(launch_apply(h, true, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
+        }
+      } else {
+        if (pc) {
+          HPS_CUDA_TRY(launch_precond(h, false, VType::C128, vj, VType::C128, k.z, k.zt, nrhs, st));
+          HPS_CUDA_TRY(launch_apply(h, false, VType::C128, k.z, VType::C128, w, nullptr, nrhs, false, st));
+        } else {
+          HPS_CUDA_TRY(launch_apply(h, false, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
+        }
+      }
+      VecArgs va;
+      va.V = k.V;
+      va.w = w;
+      va.nf = nf;
+      va.nrhs = nrhs;
+      va.nvec = j + 1;
+      va.M1 = M1;
+      va.nblk = k.nblk;
+      va.part = k.part;
+      va.active = active;
+      const dim3 bgrid(k.nblk, nrhs);
+      mdot_kernel<<<bgrid, kT, 0, st>>>(va);
+      HPS_CUDA_TRY(cudaGetLastError());
+      reduce_kernel<<<nrhs, 64, 0, st>>>(k.part, k.nblk, j + 1, M1, k.hcol, M1 + 1, 0, active);
+      HPS_CUDA_TRY(cudaGetLastError());
+      va.coef = k.hcol;
+      va.cstride = M1 + 1;
+      axpy_kernel<<<bgrid, kT, 0, st>>>(va, 1);
+      HPS_CUDA_TRY(cudaGetLastError());
+      reduce_kernel<<<nrhs, 64, 0, st>>>(k.part, k.nblk, j + 1, M1, h2, M1, 0, active);
+      HPS_CUDA_TRY(cudaGetLastError());
+      va.coef = h2;
+      va.cstride = M1;
+      axpy_kernel<<<bgrid, kT, 0, st>>>(va, 2);
+      HPS_CUDA_TRY(cudaGetLastError());
+      HPS_CUDA_TRY(cudaMemsetAsync(any_active, 0, sizeof(int), st));
+      GivensArgs ga;
+      ga.nrhs = nrhs;
+      ga.m = m;
+      ga.j = j;
+      ga.M1 = M1;
+      ga.nblk = k.nblk;
+      ga.part = k.part;
+      ga.hcol = k.hcol;
+      ga.h2 = h2;
+      ga.H = k.H;
+      ga.cs = k.cs;
+      ga.sn = k.sn;
+      ga.g = k.g;
+      ga.est = est;
+      ga.invn = invn;
+      ga.active = active;
+      ga.kcount = kcount;
+      ga.target = target;
+      ga.any_active = any_active;
+      givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(ga);
+      HPS_CUDA_TRY(cudaGetLastError());
+      scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);
+      HPS_CUDA_TRY(cudaGetLastError());
+      ++its;
+      jdone = j + 1;
+      int hany = 0;
+      HPS_CUDA_TRY(cudaMemcpyAsync(&hany, any_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      HPS_CUDA_TRY(cudaStreamSynchronize(st));
+      if (!hany) break;
+    }
+    // x += M^{-1} (V y)
+    lsq_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, m, M1, k.H, k.g, kcount, k.y);
+    HPS_CUDA_TRY(cudaGetLastError());
+    combine_kernel<<<vgrid, 256, 0, st>>>(k.V, nrhs, nf, jdone, m, k.y, k.u);
+    HPS_CUDA_TRY(cudaGetLastError());
+    const long long nall = (long long)nrhs * nf;
+    if (pc) {
+      if (mixed) {
+        HPS_CUDA_TRY(launch_precond(h, true, VType::C128, k.u, VType::C64, k.z, k.zt, nrhs, st));
+        xpy_kernel<float2><<<4 * h->nsm, 256, 0, st>>>(x, (const float2*)k.z, nall);
+      } else {
+        HPS_CUDA_TRY(launch_precond(h, false, VType::C128, k.u, VType::C128, k.z, k.zt, nrhs, st));
+        xpy_kernel<double2><<<4 * h->nsm, 256, 0, st>>>(x, (const double2*)k.z, nall);
+      }
+    } else {
+      xpy_kernel<double2><<<4 * h->nsm, 256, 0, st>>>(x, k.u, nall);
+    }
+    HPS_CUDA_TRY(cudaGetLastError());
+    // true residual with the FP64 maps
+    HPS_CUDA_TRY(launch_apply(h, false, VType::C128, x, VType::C128, k.r, b, nrhs, true, st));
+    if ((rc = vec_norms(h, k.r, nrhs, rnorm, st))) return rc;
+    ++cycles;
+  }
+  double rel = 0.0;
+  for (int r = 0; r < nrhs; ++r)
+    if (bnorm[r] > 0.0) rel = std::max(rel, rnorm[r] / bnorm[r]);
+  if (info) {
+    info->iterations = its;
+    info->cycles = cycles;
+    info->converged = converged ? 1 : 0;
+    info->rel_residual = rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!converged) {
+    set_error("GMRES did not reach the tolerance within maxit iterations");
+    return HPS_ENOCONV;
+  }
+  return HPS_OK;
+}
+
+}  // namespace hps

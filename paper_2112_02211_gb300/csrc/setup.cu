@@ -1,0 +1,811 @@
+// Setup of the HPS operators on the device (per medium, not per iteration).
+//
+// Per leaf (Sec. 2.1, eq. (leaf)): assemble the dense leaf matrix
+//   A = [ -(D_x^2 + D_y^2 + D_z^2) - C ]   interior rows
+//       [  N + i eta I(I_b, :)          ]   face rows (eq. (flux), F)
+// augmented with identity columns, and eliminate it with partial pivoting
+// (FP64).  Eliminating the last n_b pivots Gauss-Jordan style turns the
+// bottom-right block of U into I, so the boundary rows of the augmented part
+// are (A^{-1})_{b,:} directly:
+//   R_C = I - 2 i eta (A^{-1})_bb,   H_C = -2 i eta (A^{-1})_bi,
+// which follows from g = G u = F u - 2 i eta u_b (eq. (G)).  The face data is
+// then moved to Gauss points: R = P R_C P^{-1}, H = P H_C, P = blockdiag(Q (x) Q).
+//
+// Preconditioner (Sec. 4, Sec. 4.1): the same leaf maps with C replaced by
+// lambda^tau = (max + min)/2 of C over the leaf (homogenized, R~).  For every
+// cluster of leaves, J_c = I + Pi_c R~ ordered (external, internal) is
+// [[I, 0], [B, I + D]], so J_c^{-1} r needs K_c = (I + D)^{-1} (dense, inverted
+// here by the same elimination kernel) and the blocks B^beta of R~ (internal
+// rows, external columns of each leaf).
+#include <algorithm>
+#include <type_traits>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxP = 16;
+
+// ---------------------------------------------------------------------------
+// 1D tables: Chebyshev extreme points, differentiation matrices (Sec. 2.1),
+// Gauss-Legendre points by Newton's method on the Legendre recurrence, the
+// Lagrange interpolation Q from interior Chebyshev points to Gauss points and
+// its inverse.  One thread; p <= 16.
+// ---------------------------------------------------------------------------
+__global__ void tables_kernel(double* T, TableLayout tl, double hx, double hy, double hz) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int p = tl.p, q = tl.q;
+  double* x = T + tl.x;
+  for (int j = 0; j < p; ++j) x[j] = -cos(kPi * (double)j / (double)(p - 1));
+  double Dr[kMaxP * kMaxP];
+  for (int i = 0; i < p; ++i) {
+    double ci = (i == 0 || i == p - 1) ? 2.0 : 1.0;
+    double rs = 0.0;
+    for (int j = 0; j < p; ++j) {
+      if (j == i) continue;
+      double cj = (j == 0 || j == p - 1) ? 2.0 : 1.0;
+      double sg = ((i + j) & 1) ? -1.0 : 1.0;
+      double v = (ci / cj) * sg / (x[i] - x[j]);
+      Dr[i * p + j] = v;
+      rs += v;
+    }
+    Dr[i * p + i] = -rs;
+  }
+  const double hh[3] = {hx, hy, hz};
+  for (int a = 0; a < 3; ++a) {
+    double* D = T + tl.D + a * p * p;
+    double s = 2.0 / hh[a];
+    for (int i = 0; i < p * p; ++i) D[i] = s * Dr[i];
+    double* D2 = T + tl.D2 + a * p * p;
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) {
+        double acc = 0.0;
+        for (int m = 0; m < p; ++m) acc += D[i * p + m] * D[m * p + j];
+        D2[i * p + j] = acc;
+      }
+  }
+  // Gauss-Legendre nodes: Newton iteration from the standard cosine guesses.
+  double* xg = T + tl.xg;
+  double* wg = T + tl.wg;
+  for (int i = 0; i < q; ++i) {
+    double z = cos(kPi * (i + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < q; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (q == 1) { p1 = z; p0 = 1.0; }
+      dp = q * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < q; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = q * (z * p1 - p0) / (z * z - 1.0);
+    }
+    xg[q - 1 - i] = z;  // guesses run from +1 downwards; store ascending
+    wg[q - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  // Q[a][j]: Lagrange basis j of the interior Chebyshev points x[1..p-2] at xg[a].
+  double* Q = T + tl.Q;
+  for (int a = 0; a < q; ++a)
+    for (int j = 0; j < q; ++j) {
+      double v = 1.0;
+      for (int m = 0; m < q; ++m)
+        if (m != j) v *= (xg[a] - x[m + 1]) / (x[j + 1] - x[m + 1]);
+      Q[a * q + j] = v;
+    }
+  // Qi = Q^{-1} by Gauss-Jordan with partial pivoting.
+  double Wm[kMaxP * 2 * kMaxP];
+  const int w2 = 2 * q;
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < w2; ++j) Wm[i * w2 + j] = (j < q) ? Q[i * q + j] : (j - q == i ? 1.0 : 0.0);
+  for (int k = 0; k < q; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < q; ++r)
+      if (fabs(Wm[r * w2 + k]) > fabs(Wm[piv * w2 + k])) piv = r;
+    if (piv != k)
+      for (int j = 0; j < w2; ++j) {
+        double t = Wm[k * w2 + j];
+        Wm[k * w2 + j] = Wm[piv * w2 + j];
+        Wm[piv * w2 + j] = t;
+      }
+    double inv = 1.0 / Wm[k * w2 + k];
+    for (int j = 0; j < w2; ++j) Wm[k * w2 + j] *= inv;
+    for (int r = 0; r < q; ++r) {
+      if (r == k) continue;
+      double m = Wm[r * w2 + k];
+      if (m == 0.0) continue;
+      for (int j = 0; j < w2; ++j) Wm[r * w2 + j] -= m * Wm[k * w2 + j];
+    }
+  }
+  double* Qi = T + tl.Qi;
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) Qi[i * q + j] = Wm[i * w2 + q + j];
+}
+
+// ---------------------------------------------------------------------------
+// Node coordinates.
+// ---------------------------------------------------------------------------
+__global__ void nodes_kernel(const double* T, TableLayout tl, int nx, int ny, int nz, double* xi,
+                             double* xf) {
+  const int p = tl.p, q = tl.q, n1 = p - 2;
+  const long long nl = (long long)nx * ny * nz;
+  const long long ni = (long long)n1 * n1 * n1, nb = 6LL * q * q;
+  const double h[3] = {1.0 / nx, 1.0 / ny, 1.0 / nz};
+  const double* x = T + tl.x;
+  const double* xg = T + tl.xg;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = tid; t < nl * (ni > nb ? ni : nb); t += stride) {
+    long long leaf = t / (ni > nb ? ni : nb);
+    long long r = t % (ni > nb ? ni : nb);
+    int ix = (int)(leaf % nx), iy = (int)((leaf / nx) % ny), iz = (int)(leaf / ((long long)nx * ny));
+    double c[3] = {ix * h[0], iy * h[1], iz * h[2]};
+    if (xi && r < ni) {
+      int i = (int)(r % n1) + 1, j = (int)((r / n1) % n1) + 1, k = (int)(r / ((long long)n1 * n1)) + 1;
+      double* o = xi + 3 * (leaf * ni + r);
+      o[0] = c[0] + 0.5 * h[0] * (x[i] + 1.0);
+      o[1] = c[1] + 0.5 * h[1] * (x[j] + 1.0);
+      o[2] = c[2] + 0.5 * h[2] * (x[k] + 1.0);
+    }
+    if (xf && r < nb) {
+      int face = (int)(r / (q * q)), jj = (int)(r % (q * q));
+      int j1 = jj % q, j2 = jj / q;
+      int axis = face >> 1;
+      int a0 = (axis == 0) ? 1 : 0, a1 = (axis == 2) ? 1 : 2;
+      double* o = xf + 3 * (leaf * nb + r);
+      o[axis] = c[axis] + ((face & 1) ? h[axis] : 0.0);
+      o[a0] = c[a0] + 0.5 * h[a0] * (xg[j1] + 1.0);
+      o[a1] = c[a1] + 0.5 * h[a1] * (xg[j2] + 1.0);
+    }
+  }
+}
+
+// Local index of grid node (i, j, k), 0 <= i,j,k < p, not on an edge/corner.
+__device__ __forceinline__ int gidx(int i, int j, int k, int p, int n1, int ni) {
+  const int last = p - 1;
+  const bool bi = (i == 0 || i == last), bj = (j == 0 || j == last), bk = (k == 0 || k == last);
+  if (!bi && !bj && !bk) return (i - 1) + n1 * ((j - 1) + n1 * (k - 1));
+  int face, a, b;
+  if (bi) { face = (i == 0) ? 0 : 1; a = j; b = k; }
+  else if (bj) { face = (j == 0) ? 2 : 3; a = i; b = k; }
+  else { face = (k == 0) ? 4 : 5; a = i; b = j; }
+  return ni + face * n1 * n1 + (a - 1) + n1 * (b - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Leaf matrix assembly into a zeroed row-major workspace (one thread per row).
+// Columns [0, n): A; [n, n+nb): e_{boundary}; [n+nb, n+nb+ni): e_{interior}
+// (only when with_h).  Interior rows take C from cdiag, or the leaf constant
+// lam[leaf] for the homogenized operator.
+// ---------------------------------------------------------------------------
+__global__ void assemble_kernel(double2* W, long long wstride, int ld, const int* leaf_ids, int leaf0,
+                                int nbatch, const double* T, TableLayout tl, double eta,
+                                const double2* cdiag, const double2* lam, int with_h) {
+  const int p = tl.p, n1 = p - 2, ni = n1 * n1 * n1, nb = 6 * n1 * n1, n = ni + nb;
+  const int b = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbatch || r >= n) return;
+  const int leaf = leaf_ids ? leaf_ids[b] : leaf0 + b;
+  double2* row = W + (long long)b * wstride + (long long)r * ld;
+  const double* D = T + tl.D;
+  const double* D2 = T + tl.D2;
+  if (r < ni) {
+    const int i = r % n1 + 1, j = (r / n1) % n1 + 1, k = r / (n1 * n1) + 1;
+    for (int m = 0; m < p; ++m) {
+      row[gidx(m, j, k, p, n1, ni)].x -= D2[0 * p * p + i * p + m];
+      row[gidx(i, m, k, p, n1, ni)].x -= D2[1 * p * p + j * p + m];
+      row[gidx(i, j, m, p, n1, ni)].x -= D2[2 * p * p + k * p + m];
+    }
+    const double2 c = lam ? lam[leaf] : cdiag[(long long)leaf * ni + r];
+    row[r].x -= c.x;
+    row[r].y -= c.y;
+    if (with_h) row[n + nb + r].x = 1.0;
+  } else {
+    const int jb = r - ni;
+    const int face = jb / (n1 * n1), rem = jb % (n1 * n1);
+    const int a = rem % n1 + 1, bb = rem / n1 + 1;
+    const int axis = face >> 1;
+    const int e = (face & 1) ? p - 1 : 0;
+    const double sg = (face & 1) ? 1.0 : -1.0;
+    int pt[3];
+    pt[axis] = e;
+    pt[axis == 0 ? 1 : 0] = a;
+    pt[axis == 2 ? 1 : 2] = bb;
+    for (int m = 0; m < p; ++m) {
+      int q3[3] = {pt[0], pt[1], pt[2]};
+      q3[axis] = m;
+      row[gidx(q3[0], q3[1], q3[2], p, n1, ni)].x += sg * D[axis * p * p + e * p + m];
+    }
+    row[r].y += eta;
+    row[n + jb].x = 1.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched elimination with partial pivoting, one CTA per matrix (row-major,
+// n rows, ncols >= n columns).  Pivots k >= gj0 also eliminate the rows
+// [gj0, k) above them, so on exit rows [gj0, n) of columns [n, ncols) hold
+// the corresponding rows of A^{-1} E.  A zero pivot sets *status = 1.
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) gj_kernel(double2* W, long long wstride, int ld, int n, int ncols,
+                                                int gj0, int nbatch, int* status) {
+  extern __shared__ double2 prow[];
+  __shared__ double sval[NT / 32];
+  __shared__ int sidx[NT / 32];
+  __shared__ int piv_s;
+  if ((int)blockIdx.x >= nbatch) return;
+  double2* M = W + (long long)blockIdx.x * wstride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int r = k + tid; r < n; r += NT) {
+      double2 v = M[(long long)r * ld + k];
+      double a = fabs(v.x) + fabs(v.y);
+      if (a > best) { best = a; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { sval[warp] = best; sidx[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = (lane < NT / 32) ? sval[lane] : -1.0;
+      bi = (lane < NT / 32) ? sidx[lane] : n;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (!(best > 0.0) || bi >= n) {
+          atomicExch(status, 1);
+          bi = k;
+        }
+        piv_s = bi;
+      }
+    }
+    __syncthreads();
+    const int piv = piv_s;
+    double2 pv = M[(long long)piv * ld + k];
+    double2 inv = (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0.0, 0.0) : cinv(pv);
+    for (int c = k + tid; c < ncols; c += NT) {
+      double2 a = M[(long long)piv * ld + c];
+      if (piv != k) M[(long long)piv * ld + c] = M[(long long)k * ld + c];
+      a = cmul(a, inv);
+      prow[c] = a;
+      M[(long long)k * ld + c] = a;
+    }
+    __syncthreads();
+    const int lo = (k >= gj0) ? gj0 : k + 1;
+    for (int r = lo + warp; r < n; r += NT / 32) {
+      if (r == k) continue;
+      double2* Mr = M + (long long)r * ld;
+      const double2 m = Mr[k];
+      if (m.x == 0.0 && m.y == 0.0) continue;
+      for (int c = k + 1 + lane; c < ncols; c += 32) {
+        const double2 u = prow[c];
+        double2 v = Mr[c];
+        v.x -= m.x * u.x - m.y * u.y;
+        v.y -= m.x * u.y + m.y * u.x;
+        Mr[c] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// R_C = I - 2 i eta X_bb and (optionally) H_C = -2 i eta X_bi from the
+// eliminated workspace, written to per-leaf storage with leading dims ldr/ldh.
+__global__ void extract_kernel(const double2* W, long long wstride, int ld, int n, int ni, int nb,
+                               double eta, int nbatch, double2* R, long long rstride, int ldr,
+                               double2* H, long long hstride, int ldh) {
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  const int ncols_out = nb + (H ? ni : 0);
+  const double2* Wb = W + (long long)b * wstride;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nb * ncols_out;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int jb = (int)(t / ncols_out), c = (int)(t % ncols_out);
+    const double2 v = Wb[(long long)(ni + jb) * ld + n + c];
+    // -2 i eta (v.x + i v.y) = 2 eta v.y - 2 i eta v.x
+    double2 o = make_double2(2.0 * eta * v.y, -2.0 * eta * v.x);
+    if (c < nb) {
+      if (c == jb) o.x += 1.0;
+      R[(long long)b * rstride + (long long)jb * ldr + c] = o;
+    } else {
+      H[(long long)b * hstride + (long long)jb * ldh + (c - nb)] = o;
+    }
+  }
+}
+
+// In-place S <- A S A^T on q x q segments of a batch of matrices.
+// mode 0: segment (row r, block f) = M[r][f q^2 + j]; mode 1: (col c, block f)
+// = M[f q^2 + j][c].  A = Q (trans = 0) or Q^{-T} (trans = 1; from Qi).
+__global__ void seg_kron_kernel(double2* M, long long mstride, int ld, int nrows, int ncols, int nbatch,
+                                const double* T, TableLayout tl, int trans, int mode) {
+  extern __shared__ double2 sm[];
+  const int q = tl.q, q2 = q * q;
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double2* S = sm + warp * 2 * q2;
+  double2* T1 = S + q2;
+  const double* Am = T + (trans ? tl.Qi : tl.Q);
+  const long long nseg_per = (mode == 0) ? (long long)nrows * (ncols / q2) : (long long)ncols * (nrows / q2);
+  const long long nseg = nseg_per * nbatch;
+  for (long long s = (long long)blockIdx.x * warps + warp; s < nseg; s += (long long)gridDim.x * warps) {
+    const long long b = s / nseg_per, sl = s % nseg_per;
+    double2* base = M + b * mstride;
+    long long off;
+    long long es;
+    if (mode == 0) {
+      const int nf = ncols / q2;
+      const long long r = sl / nf;
+      const int f = (int)(sl % nf);
+      off = r * ld + (long long)f * q2;
+      es = 1;
+    } else {
+      const long long c = sl % ncols;
+      const int f = (int)(sl / ncols);
+      off = (long long)f * q2 * ld + c;
+      es = ld;
+    }
+    for (int j = lane; j < q2; j += 32) S[j] = base[off + j * es];
+    __syncwarp();
+    // T1[j2][a] = sum_j1 S[j2][j1] A(a, j1)
+    for (int e = lane; e < q2; e += 32) {
+      const int j2 = e / q, a = e % q;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int j1 = 0; j1 < q; ++j1) {
+        const double av = trans ? Am[j1 * q + a] : Am[a * q + j1];
+        acc.x += S[j2 * q + j1].x * av;
+        acc.y += S[j2 * q + j1].y * av;
+      }
+      T1[e] = acc;
+    }
+    __syncwarp();
+    // out[bq][a] = sum_j2 A(bq, j2) T1[j2][a]
+    for (int e = lane; e < q2; e += 32) {
+      const int bq = e / q, a = e % q;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int j2 = 0; j2 < q; ++j2) {
+        const double av = trans ? Am[j2 * q + bq] : Am[bq * q + j2];
+        acc.x += av * T1[j2 * q + a].x;
+        acc.y += av * T1[j2 * q + a].y;
+      }
+      base[off + e * es] = acc;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void cast_kernel(const double2* in, float2* out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void cdiag_kernel(const double2* b, double kappa, long long count, double2* c) {
+  const double k2 = kappa * kappa;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    c[i] = make_double2(k2 * (1.0 - b[i].x), -k2 * b[i].y);
+}
+
+// lambda^tau = (max + min)/2 of C over the leaf, real and imaginary parts separately.
+__global__ void lambda_kernel(const double2* c, int ni, double2* lam) {
+  const int leaf = blockIdx.x;
+  double mxr = -1e300, mnr = 1e300, mxi = -1e300, mni = 1e300;
+  for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+    double2 v = c[(long long)leaf * ni + i];
+    mxr = fmax(mxr, v.x); mnr = fmin(mnr, v.x);
+    mxi = fmax(mxi, v.y); mni = fmin(mni, v.y);
+  }
+  __shared__ double s[4][32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mxr = fmax(mxr, __shfl_xor_sync(0xffffffffu, mxr, o));
+    mnr = fmin(mnr, __shfl_xor_sync(0xffffffffu, mnr, o));
+    mxi = fmax(mxi, __shfl_xor_sync(0xffffffffu, mxi, o));
+    mni = fmin(mni, __shfl_xor_sync(0xffffffffu, mni, o));
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) { s[0][warp] = mxr; s[1][warp] = mnr; s[2][warp] = mxi; s[3][warp] = mni; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      mxr = fmax(mxr, s[0][w]); mnr = fmin(mnr, s[1][w]);
+      mxi = fmax(mxi, s[2][w]); mni = fmin(mni, s[3][w]);
+    }
+    lam[leaf] = make_double2(0.5 * (mxr + mnr), 0.5 * (mxi + mni));
+  }
+}
+
+// B^leaf = R~^leaf[internal face rows][external face cols] for the leaves of a batch.
+__global__ void extract_b_kernel(const double2* Rt, long long rstride, int ldr, const int* leaf_ids,
+                                 int nbatch, int q, const uint8_t* int_mask, const long long* b_off,
+                                 double2* B64, float2* B32) {
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  const int leaf = leaf_ids[b];
+  const int q2 = q * q;
+  const unsigned mask = int_mask[leaf];
+  const int nint = __popc(mask), next = 6 - nint;
+  if (nint == 0) return;
+  int ifaces[6], efaces[6];
+  int a = 0, e = 0;
+  for (int f = 0; f < 6; ++f) {
+    if (mask & (1u << f)) ifaces[a++] = f; else efaces[e++] = f;
+  }
+  const int ldb = (int)rup4(next * q2);
+  const long long off = b_off[leaf];
+  const long long total = (long long)nint * q2 * next * q2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / (next * q2)), c = (int)(t % (next * q2));
+    const int rf = ifaces[r / q2], cf = efaces[c / q2];
+    const double2 v = Rt[(long long)b * rstride + (long long)(rf * q2 + r % q2) * ldr + cf * q2 + c % q2];
+    const long long o = off + (long long)r * ldb + c;
+    if (B64) B64[o] = v;
+    if (B32) B32[o] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// [I + D | I] for each cluster of a batch (row-major, ld = ldw); D couples
+// internal slot a (leaf alpha, face k) to the slots of beta = nbr(alpha, k)
+// through R~^beta's rows on face k^1.
+__global__ void assemble_cluster_kernel(double2* W, long long wstride, int ldw, int cl0, int nbatch,
+                                        const int* cl_slot_begin, const int* slot_lf,
+                                        const int* cl_leaf_begin, const int* cl_leaves,
+                                        const double2* Rt, long long rstride, int ldr, int leafpos0,
+                                        GridDims g, int q) {
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  const int c = cl0 + b;
+  const int q2 = q * q;
+  const int s0 = cl_slot_begin[c], ns = cl_slot_begin[c + 1] - s0;
+  const int nint = ns * q2;
+  const int lb = cl_leaf_begin[c], le = cl_leaf_begin[c + 1];
+  double2* Wb = W + (long long)b * wstride;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nint * nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t / nint), col = (int)(t % nint);
+    const int sa = row / q2, ja = row % q2;
+    const int sb = col / q2, jb = col % q2;
+    const int lfa = slot_lf[s0 + sa], lfb = slot_lf[s0 + sb];
+    const int alpha = lfa / 6, ka = lfa % 6;
+    const int beta_b = lfb / 6, kb = lfb % 6;
+    double2 v = make_double2(row == col ? 1.0 : 0.0, 0.0);
+    const int beta = g.neighbor(alpha, ka);
+    if (beta == beta_b) {
+      int pos = -1;
+      for (int l = lb; l < le; ++l)
+        if (cl_leaves[l] == beta) pos = l - leafpos0;
+      const double2 r = Rt[(long long)pos * rstride + (long long)((ka ^ 1) * q2 + ja) * ldr + kb * q2 + jb];
+      v.x += r.x;
+      v.y += r.y;
+    }
+    Wb[(long long)row * ldw + col] = v;
+    Wb[(long long)row * ldw + nint + col] = make_double2(row == col ? 1.0 : 0.0, 0.0);
+  }
+}
+
+__global__ void extract_kc_kernel(const double2* W, long long wstride, int ldw, int cl0, int nbatch,
+                                  const int* cl_slot_begin, const long long* kc_off, int q, double2* K64,
+                                  float2* K32) {
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  const int c = cl0 + b;
+  const int q2 = q * q;
+  const int nint = (cl_slot_begin[c + 1] - cl_slot_begin[c]) * q2;
+  const int ldk = (int)rup4(nint);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nint * nint;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t / nint), col = (int)(t % nint);
+    const double2 v = W[(long long)b * wstride + (long long)row * ldw + nint + col];
+    const long long o = kc_off[c] + (long long)row * ldk + col;
+    if (K64) K64[o] = v;
+    if (K32) K32[o] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_tables(double* tables, const TableLayout& tl, double hx, double hy, double hz,
+                          cudaStream_t st) {
+  tables_kernel<<<1, 32, 0, st>>>(tables, tl, hx, hy, hz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cdiag(const double2* b, double kappa, long long count, double2* c, cudaStream_t st) {
+  cdiag_kernel<<<1024, 256, 0, st>>>(b, kappa, count, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nodes(const double* tables, const TableLayout& tl, int nx, int ny, int nz,
+                         double* xi, double* xf, cudaStream_t st) {
+  nodes_kernel<<<1024, 256, 0, st>>>(tables, tl, nx, ny, nz, xi, xf);
+  return cudaGetLastError();
+}
+
+namespace {
+
+constexpr int kGjThreads = 512;
+
+cudaError_t run_gj(double2* W, long long wstride, int ld, int n, int ncols, int gj0, int nbatch, int* status,
+                   cudaStream_t st) {
+  const size_t smem = (size_t)ncols * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(gj_kernel<kGjThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  gj_kernel<kGjThreads><<<nbatch, kGjThreads, smem, st>>>(W, wstride, ld, n, ncols, gj0, nbatch, status);
+  return cudaGetLastError();
+}
+
+cudaError_t run_seg_kron(double2* M, long long mstride, int ld, int nrows, int ncols, int nbatch,
+                         const double* T, const TableLayout& tl, int trans, int mode, int nsm, cudaStream_t st) {
+  const int q2 = tl.q * tl.q;
+  const size_t smem = 8 * 2 * q2 * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(seg_kron_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  seg_kron_kernel<<<nsm * 8, 256, smem, st>>>(M, mstride, ld, nrows, ncols, nbatch, T, tl, trans, mode);
+  return cudaGetLastError();
+}
+
+// Device status word + copy-back helper.
+int check_status(int* d_status, cudaStream_t st, const char* what) {
+  int hs = 0;
+  HPS_CUDA_TRY(cudaMemcpyAsync(&hs, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hs != 0) {
+    set_error(std::string(what) + ": zero pivot in the elimination");
+    return HPS_EBREAKDOWN;
+  }
+  return HPS_OK;
+}
+
+size_t workspace_budget(const hps_handle* h) {
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  size_t cap = (size_t)24 << 30;
+  size_t b = fr / 3;
+  return b < cap ? b : cap;
+}
+
+}  // namespace
+
+int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+  const int n = h->n, ni = h->ni, nb = h->nb;
+  const int ncols = n + nb + ni;
+  const int ld = ncols;
+  const long long wstride = (long long)n * ld;
+  const size_t per = (size_t)wstride * sizeof(double2);
+  int nbatch = (int)std::min<size_t>((size_t)h->nl, std::max<size_t>(1, workspace_budget(h) / per));
+  nbatch = std::min(nbatch, 4 * h->nsm);
+  double2* W = nullptr;
+  int* d_status = nullptr;
+  HPS_CUDA_TRY(cudaMalloc(&W, per * nbatch));
+  HPS_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
+  HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  int rc = HPS_OK;
+  for (int l0 = 0; l0 < h->nl && rc == HPS_OK; l0 += nbatch) {
+    const int nbt = std::min(nbatch, h->nl - l0);
+    auto body = [&]() -> int {
+      HPS_CUDA_TRY(cudaMemsetAsync(W, 0, per * nbt, st));
+      dim3 ga((n + 127) / 128, nbt);
+      assemble_kernel<<<ga, 128, 0, st>>>(W, wstride, ld, nullptr, l0, nbt, h->tables, h->tl, h->eta, cdiag,
+                                         nullptr, 1);
+      HPS_CUDA_TRY(cudaGetLastError());
+      HPS_CUDA_TRY(run_gj(W, wstride, ld, n, ncols, ni, nbt, d_status, st));
+      double2* Rb = h->R64 + (long long)l0 * nb * h->ldR;
+      double2* Hb = h->H64 + (long long)l0 * nb * h->ldH;
+      dim3 ge(256, nbt);
+      extract_kernel<<<ge, 256, 0, st>>>(W, wstride, ld, n, ni, nb, h->eta, nbt, Rb, (long long)nb * h->ldR,
+                                         h->ldR, Hb, (long long)nb * h->ldH, h->ldH);
+      HPS_CUDA_TRY(cudaGetLastError());
+      // R = P (R_C P^{-1}): rows by Q^{-T} (.) Q^{-1}, then columns by Q (.) Q^T.
+      HPS_CUDA_TRY(run_seg_kron(Rb, (long long)nb * h->ldR, h->ldR, nb, nb, nbt, h->tables, h->tl, 1, 0, h->nsm, st));
+      HPS_CUDA_TRY(run_seg_kron(Rb, (long long)nb * h->ldR, h->ldR, nb, nb, nbt, h->tables, h->tl, 0, 1, h->nsm, st));
+      HPS_CUDA_TRY(run_seg_kron(Hb, (long long)nb * h->ldH, h->ldH, nb, ni, nbt, h->tables, h->tl, 0, 1, h->nsm, st));
+      if (h->R32) {
+        const long long cnt = (long long)nbt * nb * h->ldR;
+        cast_kernel<<<1024, 256, 0, st>>>(Rb, h->R32 + (long long)l0 * nb * h->ldR, cnt);
+        HPS_CUDA_TRY(cudaGetLastError());
+      }
+      return HPS_OK;
+    };
+    rc = body();
+  }
+  if (rc == HPS_OK) rc = check_status(d_status, st, "leaf ItI maps");
+  cudaStreamSynchronize(st);
+  cudaFree(W);
+  cudaFree(d_status);
+  return rc;
+}
+
+void build_cluster_tables(hps_handle* h, int width) {
+  ClusterTables& ct = h->ct;
+  ct = ClusterTables();
+  const int q2 = h->q * h->q;
+  ct.lf_slot.assign((size_t)h->nl * 6, -1);
+  ct.int_mask.assign(h->nl, 0);
+  ct.b_off.assign(h->nl, 0);
+  ct.cl_leaf_begin.push_back(0);
+  ct.cl_slot_begin.push_back(0);
+  auto lid = [&](int ix, int iy, int iz) { return ix + h->nx * (iy + h->ny * iz); };
+  for (int cz = 0; cz < h->nz; cz += width)
+    for (int cy = 0; cy < h->ny; cy += width)
+      for (int cx = 0; cx < h->nx; cx += width) {
+        const int c = ct.ncl++;
+        const int x1 = std::min(cx + width, h->nx), y1 = std::min(cy + width, h->ny), z1 = std::min(cz + width, h->nz);
+        for (int iz = cz; iz < z1; ++iz)
+          for (int iy = cy; iy < y1; ++iy)
+            for (int ix = cx; ix < x1; ++ix) ct.cl_leaves.push_back(lid(ix, iy, iz));
+        for (int iz = cz; iz < z1; ++iz)
+          for (int iy = cy; iy < y1; ++iy)
+            for (int ix = cx; ix < x1; ++ix) {
+              const int leaf = lid(ix, iy, iz);
+              const int c3[3] = {ix, iy, iz}, lo3[3] = {cx, cy, cz}, hi3[3] = {x1, y1, z1};
+              for (int f = 0; f < 6; ++f) {
+                const int axis = f >> 1, d = (f & 1) ? 1 : -1;
+                const int v = c3[axis] + d;
+                if (v < lo3[axis] || v >= hi3[axis]) continue;
+                const int slot = ct.nslots++;
+                ct.slot_lf.push_back(leaf * 6 + f);
+                ct.slot_cluster.push_back(c);
+                ct.lf_slot[(size_t)leaf * 6 + f] = slot;
+                ct.int_mask[leaf] |= (uint8_t)(1u << f);
+              }
+            }
+        ct.cl_leaf_begin.push_back((int)ct.cl_leaves.size());
+        ct.cl_slot_begin.push_back(ct.nslots);
+      }
+  ct.cl_kc_off.resize(ct.ncl);
+  long long off = 0;
+  for (int c = 0; c < ct.ncl; ++c) {
+    const long long nint = (long long)(ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2;
+    ct.cl_kc_off[c] = off;
+    off += nint * round_up(nint, 4);
+  }
+  ct.kc_elems = off;
+  off = 0;
+  for (int leaf = 0; leaf < h->nl; ++leaf) {
+    const int ni_ = __builtin_popcount(ct.int_mask[leaf]);
+    ct.b_off[leaf] = off;
+    off += (long long)ni_ * q2 * round_up((long long)(6 - ni_) * q2, 4);
+  }
+  ct.b_elems = off;
+}
+
+int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+  ClusterTables& ct = h->ct;
+  const int n = h->n, ni = h->ni, nb = h->nb, q = h->q, q2 = q * q;
+  // device copies of the tables
+  auto up = [&](auto*& dst, const auto& vec) -> int {
+    using T = std::remove_reference_t<decltype(vec[0])>;
+    const size_t bytes = std::max<size_t>(1, vec.size()) * sizeof(T);
+    HPS_CUDA_TRY(cudaMalloc((void**)&dst, bytes));
+    h->bytes += bytes;
+    if (!vec.empty()) HPS_CUDA_TRY(cudaMemcpyAsync((void*)dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return HPS_OK;
+  };
+  int rc;
+  if ((rc = up(h->dct.slot_lf, ct.slot_lf))) return rc;
+  if ((rc = up(h->dct.slot_cluster, ct.slot_cluster))) return rc;
+  if ((rc = up(h->dct.cl_slot_begin, ct.cl_slot_begin))) return rc;
+  if ((rc = up(h->dct.cl_kc_off, ct.cl_kc_off))) return rc;
+  if ((rc = up(h->dct.lf_slot, ct.lf_slot))) return rc;
+  if ((rc = up(h->dct.int_mask, ct.int_mask))) return rc;
+  if ((rc = up(h->dct.b_off, ct.b_off))) return rc;
+  int* d_cl_leaf_begin = nullptr;
+  int* d_cl_leaves = nullptr;
+  HPS_CUDA_TRY(cudaMalloc(&d_cl_leaf_begin, ct.cl_leaf_begin.size() * sizeof(int)));
+  HPS_CUDA_TRY(cudaMalloc(&d_cl_leaves, ct.cl_leaves.size() * sizeof(int)));
+  HPS_CUDA_TRY(cudaMemcpyAsync(d_cl_leaf_begin, ct.cl_leaf_begin.data(), ct.cl_leaf_begin.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, st));
+  HPS_CUDA_TRY(cudaMemcpyAsync(d_cl_leaves, ct.cl_leaves.data(), ct.cl_leaves.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, st));
+
+  lambda_kernel<<<h->nl, 256, 0, st>>>(cdiag, ni, h->lambda);
+  HPS_CUDA_TRY(cudaGetLastError());
+
+  // batch sizes: clusters per batch limited by the two workspaces
+  int max_int = 0, max_leaves = 0;
+  for (int c = 0; c < ct.ncl; ++c) {
+    max_int = std::max(max_int, (ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2);
+    max_leaves = std::max(max_leaves, ct.cl_leaf_begin[c + 1] - ct.cl_leaf_begin[c]);
+  }
+  const int ncols_l = n + nb, ld_l = ncols_l;
+  const long long wl_stride = (long long)n * ld_l;
+  const int ldw = std::max(2, 2 * max_int);
+  const long long wc_stride = (long long)std::max(1, max_int) * ldw;
+  const size_t per_cluster = ((size_t)wl_stride * max_leaves + (size_t)nb * h->ldR * max_leaves + (size_t)wc_stride) *
+                             sizeof(double2);
+  int cb = (int)std::min<size_t>((size_t)ct.ncl, std::max<size_t>(1, workspace_budget(h) / per_cluster));
+  cb = std::min(cb, std::max(1, 2 * h->nsm));
+  double2 *Wl = nullptr, *Rt = nullptr, *Wc = nullptr;
+  int* d_status = nullptr;
+  int* d_leafids = nullptr;
+  HPS_CUDA_TRY(cudaMalloc(&Wl, (size_t)wl_stride * max_leaves * cb * sizeof(double2)));
+  HPS_CUDA_TRY(cudaMalloc(&Rt, (size_t)nb * h->ldR * max_leaves * cb * sizeof(double2)));
+  HPS_CUDA_TRY(cudaMalloc(&Wc, (size_t)wc_stride * cb * sizeof(double2)));
+  HPS_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
+  HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  GridDims gd{h->nx, h->ny, h->nz};
+  for (int c0 = 0; c0 < ct.ncl && rc == HPS_OK; c0 += cb) {
+    const int nc = std::min(cb, ct.ncl - c0);
+    const int lb = ct.cl_leaf_begin[c0], le = ct.cl_leaf_begin[c0 + nc];
+    const int nlb = le - lb;
+    const int* leaf_ids = d_cl_leaves + lb;
+    auto body = [&]() -> int {
+      HPS_CUDA_TRY(cudaMemsetAsync(Wl, 0, (size_t)wl_stride * nlb * sizeof(double2), st));
+      dim3 ga((n + 127) / 128, nlb);
+      assemble_kernel<<<ga, 128, 0, st>>>(Wl, wl_stride, ld_l, leaf_ids, 0, nlb, h->tables, h->tl, h->eta,
+                                          cdiag, h->lambda, 0);
+      HPS_CUDA_TRY(cudaGetLastError());
+      HPS_CUDA_TRY(run_gj(Wl, wl_stride, ld_l, n, ncols_l, ni, nlb, d_status, st));
+      dim3 ge(256, nlb);
+      extract_kernel<<<ge, 256, 0, st>>>(Wl, wl_stride, ld_l, n, ni, nb, h->eta, nlb, Rt, (long long)nb * h->ldR,
+                                         h->ldR, nullptr, 0, 0);
+      HPS_CUDA_TRY(cudaGetLastError());
+      HPS_CUDA_TRY(run_seg_kron(Rt, (long long)nb * h->ldR, h->ldR, nb, nb, nlb, h->tables, h->tl, 1, 0, h->nsm, st));
+      HPS_CUDA_TRY(run_seg_kron(Rt, (long long)nb * h->ldR, h->ldR, nb, nb, nlb, h->tables, h->tl, 0, 1, h->nsm, st));
+      extract_b_kernel<<<dim3(64, nlb), 256, 0, st>>>(Rt, (long long)nb * h->ldR, h->ldR, leaf_ids, nlb, q,
+                                                      h->dct.int_mask, h->dct.b_off, h->B64, h->B32);
+      HPS_CUDA_TRY(cudaGetLastError());
+      assemble_cluster_kernel<<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
+                                                             h->dct.slot_lf, d_cl_leaf_begin, d_cl_leaves, Rt,
+                                                             (long long)nb * h->ldR, h->ldR, lb, gd, q);
+      HPS_CUDA_TRY(cudaGetLastError());
+      // all clusters of a batch share max_int only when they have equal size; run per distinct size
+      int cstart = c0;
+      while (cstart < c0 + nc) {
+        const int sz = (ct.cl_slot_begin[cstart + 1] - ct.cl_slot_begin[cstart]) * q2;
+        int cend = cstart + 1;
+        while (cend < c0 + nc && (ct.cl_slot_begin[cend + 1] - ct.cl_slot_begin[cend]) * q2 == sz) ++cend;
+        if (sz > 0)
+          HPS_CUDA_TRY(run_gj(Wc + (long long)(cstart - c0) * wc_stride, wc_stride, ldw, sz, 2 * sz, 0, cend - cstart,
+                              d_status, st));
+        cstart = cend;
+      }
+      extract_kc_kernel<<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
+                                                       h->dct.cl_kc_off, q, h->Kc64, h->Kc32);
+      HPS_CUDA_TRY(cudaGetLastError());
+      return HPS_OK;
+    };
+    rc = body();
+  }
+  if (rc == HPS_OK) rc = check_status(d_status, st, "preconditioner blocks");
+  cudaStreamSynchronize(st);
+  cudaFree(Wl);
+  cudaFree(Rt);
+  cudaFree(Wc);
+  cudaFree(d_status);
+  cudaFree(d_cl_leaf_begin);
+  cudaFree(d_cl_leaves);
+  return rc;
+}
+
+}  // namespace hps

@@ -1,0 +1,198 @@
+"""CUDA path vs the CPU oracle, element by element on the same seeded inputs.
+
+Tolerances (relative l2 unless stated):
+* leaf maps R, H (FP64 elimination on both sides, different pivot/rounding
+  order): 1e-11;
+* hps_apply / hps_rhs in FP64: 1e-11 (dominated by the R difference above);
+  complex FP32 apply: 2e-6 (FP32 storage of R, ~6e-8 per entry, summed over
+  6 q^2 terms with FP32 accumulation);
+* hps_precond: FP64 1e-9 (the cluster inverse amplifies the map difference by
+  cond(I + D)); FP32 2e-5;
+* solves: FP64 form 1e-10, mixed form 1e-6 (the stated targets).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_cases import OracleCase, gpu_inputs, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+hps = pytest.importorskip("paper_2112_02211_gb300")
+
+
+def _ragged_workload():
+    # 3 x 2 x 2 leaves: an odd axis (clusters of width 1 and 2), p = 7 (q = 5,
+    # 6 q^2 = 150 columns: ragged tails for the 2-complex-per-lane FP32 loads).
+    w = W.manufactured(L=2, p=7, kappa=9.0)
+    w.nx, w.ny, w.nz = 3, 2, 2
+    return w
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    w = _ragged_workload()
+    oc = OracleCase(w)
+    xi, xf, b, s, t = gpu_inputs(w, hps)
+    solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b, max_rhs=4)
+    yield w, oc, solver, (xi, xf, b, s, t)
+    solver.close()
+
+
+def test_nodes_match_oracle(ragged):
+    w, oc, solver, (xi, xf, b, s, t) = ragged
+    assert np.max(np.abs(xi - oc.xi)) < 1e-15
+    assert np.max(np.abs(xf - oc.xf)) < 1e-15
+
+
+def test_leaf_maps_match_oracle(ragged):
+    w, oc, solver, _ = ragged
+    for leaf in range(oc.grid.nleaves):
+        R = solver.export("R", leaf).reshape(oc.grid.nb, oc.grid.nb)
+        H = solver.export("H", leaf).reshape(oc.grid.nb, -1)
+        assert rel(R, oc.prob.R[leaf]) < 1e-11, leaf
+        assert rel(H, oc.prob.H[leaf]) < 1e-11, leaf
+
+
+def test_homogenized_lambda_matches_oracle(ragged):
+    w, oc, solver, _ = ragged
+    for leaf in range(oc.grid.nleaves):
+        lam = solver.export("lambda", leaf)[0]
+        c = O.cdiag_from_b(w.kappa, oc.b[leaf])
+        assert abs(lam - O.homogenized_lambda(c)) <= 1e-12 * abs(lam)
+
+
+def _rand(n, seed, nrhs=1):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((nrhs, n)) + 1j * rng.standard_normal((nrhs, n)))
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_apply_matches_oracle(ragged, nrhs):
+    w, oc, solver, _ = ragged
+    f = _rand(oc.grid.nf, 10 + nrhs, nrhs)
+    ref = np.stack([oc.apply(f[r]) for r in range(nrhs)])
+    y64 = solver.apply(torch.from_numpy(f.reshape(-1)).cuda()).cpu().numpy().reshape(nrhs, -1)
+    assert rel(y64, ref) < 1e-11
+    f32 = torch.from_numpy(f.reshape(-1).astype(np.complex64)).cuda()
+    y32 = solver.apply(f32).cpu().numpy().reshape(nrhs, -1)
+    ref32 = np.stack([oc.apply(f[r].astype(np.complex64).astype(np.complex128)) for r in range(nrhs)])
+    assert rel(y32, ref32) < 2e-6
+
+
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_precond_matches_oracle(ragged, nrhs):
+    w, oc, solver, _ = ragged
+    r = _rand(oc.grid.nf, 20 + nrhs, nrhs)
+    ref = np.stack([oc.M(r[i]) for i in range(nrhs)])
+    z64 = solver.precond(torch.from_numpy(r.reshape(-1)).cuda()).cpu().numpy().reshape(nrhs, -1)
+    assert rel(z64, ref) < 1e-9
+    r32 = r.astype(np.complex64)
+    ref32 = np.stack([oc.M(r32[i].astype(np.complex128)) for i in range(nrhs)])
+    z32 = solver.precond(torch.from_numpy(r32.reshape(-1)).cuda()).cpu().numpy().reshape(nrhs, -1)
+    assert rel(z32, ref32) < 2e-5
+
+
+def test_rhs_matches_oracle(ragged):
+    w, oc, solver, (xi, xf, b, s, t) = ragged
+    bg = solver.rhs(torch.from_numpy(s.reshape(-1)).cuda(), torch.from_numpy(t.reshape(-1)).cuda())
+    assert rel(bg.cpu().numpy(), oc.rhs()) < 1e-11
+
+
+@pytest.mark.parametrize("form,tol,bar", [("fp64", 1e-12, 1e-10), ("mixed", 1e-8, 1e-6)])
+def test_solve_matches_oracle(ragged, form, tol, bar):
+    w, oc, solver, (xi, xf, b, s, t) = ragged
+    f_ref = oc.solve()
+    f, info = solver.solve(s=torch.from_numpy(s.reshape(-1)).cuda(), t=torch.from_numpy(t.reshape(-1)).cuda(),
+                           tol=tol, form=form)
+    assert info["converged"], info
+    assert rel(f.cpu().numpy(), f_ref) < bar, info
+
+
+def test_solve_host_buffers_match_device_buffers(ragged):
+    w, oc, solver, (xi, xf, b, s, t) = ragged
+    f_dev, _ = solver.solve(s=torch.from_numpy(s.reshape(-1)).cuda(), t=torch.from_numpy(t.reshape(-1)).cuda(),
+                            tol=1e-12, form="fp64")
+    out = np.zeros(oc.grid.nf, dtype=np.complex128)
+    solver.solve(s=s.reshape(-1), t=t.reshape(-1), tol=1e-12, form="fp64", out=out)
+    assert np.array_equal(out, f_dev.cpu().numpy())
+
+
+def test_solve_several_rhs(ragged):
+    w, oc, solver, (xi, xf, b, s, t) = ragged
+    # three right-hand sides: the manufactured one, twice its body load, and boundary data only
+    S = np.stack([s[0], 2.0 * s[0], np.zeros_like(s[0])])
+    T = np.stack([t[0], np.zeros_like(t[0]), t[0]])
+    f, info = solver.solve(s=torch.from_numpy(S.reshape(-1)).cuda(), t=torch.from_numpy(T.reshape(-1)).cuda(),
+                           tol=1e-12, form="fp64", nrhs=3)
+    assert info["converged"]
+    f = f.cpu().numpy().reshape(3, -1)
+    M = O.dense_face_matrix(oc.grid, oc.prob.R)
+    for r in range(3):
+        ref = np.linalg.solve(M, O.rhs_face(oc.grid, oc.prob.H, S[r], T[r]))
+        assert rel(f[r], ref) < 1e-10, r
+
+
+def test_zero_rhs_gives_zero():
+    solver = hps.Solver(2, 2, 2, 6, kappa=5.0)
+    f, info = solver.solve(tol=1e-10, form="fp64")
+    assert info["converged"] and info["iterations"] == 0
+    assert not torch.any(f != 0)
+    solver.close()
+
+
+def test_single_leaf_solution_is_boundary_data():
+    w = W.plane_wave(L=1, p=6, kappa=5.0)
+    xi, xf, b, s, t = gpu_inputs(w, hps)
+    solver = hps.Solver(1, 1, 1, 6, kappa=w.kappa, eta=w.eta, b=b)
+    f, info = solver.solve(t=torch.from_numpy(t.reshape(-1)).cuda(), tol=1e-12, form="fp64")
+    assert rel(f.cpu().numpy(), t.reshape(-1)) < 1e-14
+    solver.close()
+
+
+@pytest.fixture(scope="module")
+def plane_wave_4cubed():
+    w = W.plane_wave_4cubed()
+    oc = OracleCase(w)
+    xi, xf, b, s, t = gpu_inputs(w, hps)
+    solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b)
+    yield w, oc, solver, t
+    solver.close()
+
+
+@pytest.mark.parametrize("form,bar", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_plane_wave_4cubed_solve(plane_wave_4cubed, form, bar):
+    """4^3 leaves, p = 8, kappa = eta = 10, plane wave, GMRES(50) with 2x2x2 clusters."""
+    w, oc, solver, t = plane_wave_4cubed
+    f_ref = oc.solve()
+    f, info = solver.solve(t=torch.from_numpy(t.reshape(-1)).cuda(), tol=w.tol if form == "fp64" else 1e-8,
+                           form=form)
+    assert info["converged"], info
+    f = f.cpu().numpy()
+    assert rel(f, f_ref) < bar, info
+    # and both are close to the exact impedance data of the plane wave
+    exact = w.exact_f[0](oc.xf, oc.nrm).reshape(-1)
+    assert rel(f, exact) < 1e-3
+
+
+@pytest.fixture(scope="module")
+def bump_4cubed():
+    w = W.scaled(W.bump_16cubed(), 4)
+    oc = OracleCase(w)
+    xi, xf, b, s, t = gpu_inputs(w, hps)
+    solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b)
+    yield w, oc, solver, s
+    solver.close()
+
+
+@pytest.mark.parametrize("form,tol,bar", [("fp64", 1e-11, 1e-10), ("mixed", 1e-7, 1e-6)])
+def test_bump_scaled_solve(bump_4cubed, form, tol, bar):
+    """The variable-coefficient workload (p = 10, kappa = 40, Gaussian bump and source) on 4^3 leaves."""
+    w, oc, solver, s = bump_4cubed
+    f_ref = oc.solve()
+    f, info = solver.solve(s=torch.from_numpy(s.reshape(-1)).cuda(), tol=tol, form=form)
+    assert info["converged"], info
+    assert rel(f.cpu().numpy(), f_ref) < bar, info
