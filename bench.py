@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the iterative HPS Helmholtz solver on one GB300 per rank.
+
+Workload (synthetic, seeded): 16^3 = 4096 leaves on (0,1)^3, Chebyshev order
+p = 10, q = 8 Gauss points per face edge (1,572,864 face unknowns),
+kappa = eta = 40, medium b = 1.5 exp(-160 |x - c|^2), source
+s = exp(-400 |x - x0|^2), t = 0, relative tolerance 1e-6.
+
+A step is one solve to tolerance through the C ABI: RHS build, restarted
+GMRES(50) with the leaf ItI apply + face swap, the cluster block-Jacobi
+preconditioner, CGS2 Arnoldi and FP64 restart residuals.  `value` is face
+unknowns solved per second with the inputs already in HBM (mixed form:
+complex-FP32 operators inside FP64 Krylov + FP64 restart residual); the FP64
+form and the runs without preconditioner are reported beside it.  Setup
+(leaf maps, preconditioner) is outside the timed region.
+
+--impl reference times the CPU oracle instead (see oracle/), on a bounded
+sample of the same workload.  Under torchrun each rank solves its own
+replica (no data-path collective); rank 0 prints one JSON line.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "GMRES unknowns solved/s (mixed vs FP64, rel err<=1e-6); apply GB/s; p50/p99"
+UNIT = "unknowns/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--L", type=int, default=16, help="leaves per axis (16 = the benchmark workload)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / no-preconditioner comparison runs")
+    ap.add_argument("--cpu-sample-L", type=int, default=4)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# --------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend or "nccl")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        return self._reduce(x, "max")
+
+    def sum(self, x):
+        return self._reduce(x, "sum")
+
+    def _reduce(self, x, op):
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(unknowns_per_rank, seconds_per_rank):
+    """Whole-job throughput: all ranks' unknowns over the slowest rank's time."""
+    return sum(unknowns_per_rank) / max(seconds_per_rank)
+
+
+# --------------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, flags in rows:
+            for n, f in zip(names[1:], flags[1:]):
+                if f.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------------------------
+# algorithmic bytes per launch ("Roofline")
+# --------------------------------------------------------------------------------------------
+def interior_face_pairs(L):
+    return 6 * L ** 3 - 6 * L * L
+
+
+def apply_bytes(L, q, mat_bytes, in_bytes, out_bytes):
+    """Rows of R actually read (faces with a neighbour) + f read + f read at the target + y write."""
+    nb = 6 * q * q
+    nf = L ** 3 * nb
+    return interior_face_pairs(L) * q * q * nb * mat_bytes + nf * (2 * in_bytes + out_bytes)
+
+
+def precond_bytes(L, q, mat_bytes, vec_bytes):
+    """Stage K: K_c of every 2x2x2 cluster + t read + z_int write; stage B: B blocks + r + t + z_ext."""
+    q2 = q * q
+    ncl = (L // 2) ** 3
+    nint = 24 * q2
+    kb = ncl * nint * nint * mat_bytes + ncl * nint * 2 * vec_bytes
+    nf = L ** 3 * 6 * q2
+    bb = L ** 3 * (3 * q2) * (3 * q2) * mat_bytes + nf * 3 * vec_bytes
+    return kb, bb
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def committed_traffic(kernel):
+    """ncu DRAM bytes per launch from profiles/, valid only for the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2112_02211_gb300", "csrc", "apply.cu")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        e = d.get(kernel)
+        if e and e.get("apply_cu_sha256_16") == digest:
+            return e["bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------------
+def run_gpu(args, dist):
+    import torch
+
+    import paper_2112_02211_gb300 as hps
+
+    torch.cuda.set_device(dist.local)
+    w = W.bump_16cubed(L=args.L)
+    L, p, q = w.nx, w.p, w.q
+    xi, xf = hps.nodes(L, L, L, p)
+    b = w.sample_b(xi)
+    s = w.sample_s(xi).reshape(-1)
+    t0 = time.time()
+    solver = hps.Solver(L, L, L, p, kappa=w.kappa, eta=w.eta, b=b, device=dist.local)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    nf = solver.nf
+    s_dev = torch.from_numpy(s).cuda()
+    out = torch.empty(nf, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(form, precond, steps, warmup, profile=False, clocks=None):
+        for _ in range(warmup):
+            _, info = solver.solve(s=s_dev, tol=w.tol, form=form, out=out, precond=precond)
+        solver.profile(enable=profile, reset=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = []
+        for _ in range(steps):
+            _, info = solver.solve(s=s_dev, tol=w.tol, form=form, out=out, precond=precond)
+            infos.append(info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        ck = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1) / steps
+        prof = solver.profile(enable=False, reset=True)
+        return ms, infos, prof, ck
+
+    # headline: mixed form with the preconditioner
+    clocks = Clocks(dist.local)
+    ms, infos, prof, ck = timed("mixed", True, args.steps, args.warmup, profile=True, clocks=clocks)
+    f_mixed = out.clone()
+    ms_max = dist.max(ms)
+    value = aggregate([nf * args.steps] * dist.world, [ms_max * args.steps / 1e3] * dist.world) \
+        if dist.world > 1 else nf / (ms / 1e3)
+    if dist.world > 1:
+        value = dist.world * nf / (ms_max / 1e3)
+
+    # end to end through the same call with host buffers (H2D of s, D2H of f inside)
+    s_host = s.copy()
+    f_host = np.zeros(nf, dtype=np.complex128)
+    solver.solve(s=s_host, tol=w.tol, form="mixed", out=f_host)
+    dist.barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve(s=s_host, tol=w.tol, form="mixed", out=f_host)
+    e2e_s = (time.perf_counter() - te) / args.steps
+    e2e_s = dist.max(e2e_s)
+    e2e_value = dist.world * nf / e2e_s
+
+    # comparison runs (fewer steps): FP64 form, and both forms without the preconditioner
+    compare = {}
+    if not args.no_compare:
+        for form, pc in (("fp64", True), ("mixed", False), ("fp64", False)):
+            c_ms, c_infos, c_prof, _ = timed(form, pc, 1, 1, profile=True)
+            key = f"{form}{'' if pc else '_no_precond'}"
+            compare[key] = {"unknowns_per_s": nf / (c_ms / 1e3), "ms_per_solve": c_ms,
+                            "iterations": c_infos[-1]["iterations"], "rel_residual": c_infos[-1]["rel_residual"],
+                            "phase_ms": {k: round(v, 3) for k, v in c_prof["ms"].items()}}
+            if key == "fp64":
+                compare[key]["mixed_vs_fp64_rel_diff"] = float(
+                    torch.linalg.norm(f_mixed - out).item() / torch.linalg.norm(out).item())
+
+    # roofline of the dominant kernel and of the ItI apply, from the library's events
+    pk, pk_src = peaks()
+    q2 = q * q
+    a_bytes = apply_bytes(L, q, 8, 8, 16)  # c64 maps, c64 input, c128 output
+    kb, bb = precond_bytes(L, q, 8, 8)
+    phases = {"apply": a_bytes, "precond_k": kb, "precond_b": bb}
+    kernels = {"apply": "seg_gemv_kernel<ApplyP<float2,float2,double2>,1,4>",
+               "precond_k": "seg_gemv_kernel<PrecKP<float2,float2,float2>,1,4>",
+               "precond_b": "seg_gemv_kernel<PrecBP<float2,double2,float2>,1,4>"}
+    roof = {}
+    for ph, by in phases.items():
+        cnt = prof["count"][ph]
+        if cnt:
+            dur = prof["ms"][ph] / cnt / 1e3
+            ach = by / dur / 1e9
+            roof[ph] = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s",
+                        "frac": round(ach / pk, 4), "traffic": committed_traffic(ph),
+                        "algorithmic_bytes": by, "avg_launch_ms": round(dur * 1e3, 4), "launches": cnt,
+                        "kernel": kernels[ph], "peak_source": pk_src}
+    dominant = max(roof, key=lambda k: prof["ms"][k]) if roof else None
+    iters = infos[-1]["iterations"]
+    rec = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": dist.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 operators, f64 Krylov/residual",
+        "data": "synthetic",
+        "config": {
+            "workload": f"bump_{L}cubed: {L}^3 leaves, p={p}, q={q}, kappa=eta={w.kappa:g}, "
+                        f"b=1.5exp(-160|x-c|^2), s=exp(-400|x-x0|^2), t=0, tol={w.tol:g}",
+            "form": "mixed (complex-FP32 apply/precond, FP64 CGS2 Arnoldi, FP64 restart residual)",
+            "preconditioner": "2x2x2 cluster block Jacobi, homogenized leaf maps",
+            "restart": 50,
+            "face_unknowns": nf,
+            "paper_unknowns": L ** 3 * ((p - 2) ** 3 + 6 * (p - 2) ** 2),
+            "parallelism": f"replicas x{dist.world}",
+            "l2": "inputs larger than L2 (leaf maps 4.8 GB c64 per apply)",
+            "setup_s": round(setup_s, 2),
+        },
+        "iterations": iters,
+        "cycles": infos[-1]["cycles"],
+        "rel_residual": infos[-1]["rel_residual"],
+        "paper_unknowns_per_s": dist.world * L ** 3 * ((p - 2) ** 3 + 6 * (p - 2) ** 2) / (ms_max / 1e3),
+        "phase_ms_per_solve": {k: round(v / args.steps, 3) for k, v in prof["ms"].items()},
+        "roofline": roof.get(dominant),
+        "roofline_apply": roof.get("apply"),
+        "roofline_all": roof,
+        "gpu_launches": prof["launches"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s_host.nbytes),
+                "d2h_bytes_per_step": int(f_host.nbytes)},
+        "clocks": ck,
+        "compare": compare,
+    }
+    solver.close()
+    return rec
+
+
+# --------------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# --------------------------------------------------------------------------------------------
+def oracle_sample(L_sample, steps=1, warmup=0):
+    """Oracle solve of the same workload on an L_sample^3 grid (same p, kappa, medium and
+    source): RHS build + GMRES(50) to 1e-6 without preconditioner, setup excluded.
+    Returns (unknowns/s, seconds per solve, cores)."""
+    import oracle as O
+
+    w = W.scaled(W.bump_16cubed(), L_sample)
+    g = O.Grid(L_sample, L_sample, L_sample, w.p)
+    xi = O.interior_nodes(g)
+    prob = O.build_problem(g, w.kappa, w.eta, w.sample_b(xi))
+    s = w.sample_s(xi)[0]
+
+    def one():
+        rhs = O.rhs_face(g, prob.H, s, None)
+        f, its, hist = O.gmres(lambda v: O.apply_face(g, prob.R, v), rhs, tol=w.tol, restart=50)
+        return its
+
+    for _ in range(warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = (time.perf_counter() - t0) / steps
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return g.nf / dt, dt, cores
+
+
+def cpu_baseline_record(L_sample):
+    v, dt, cores = oracle_sample(L_sample)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"bump workload scaled to {L_sample}^3 leaves (same p, kappa, medium, source): "
+                      f"oracle RHS build + GMRES(50) to 1e-6, no preconditioner, setup excluded; "
+                      f"{dt:.2f} s per solve; numpy with its default BLAS threading"}
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return None
+    v, dt, cores = oracle_sample(args.cpu_sample_L, steps=args.steps, warmup=args.warmup)
+    cb = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"bump workload scaled to {args.cpu_sample_L}^3 leaves (same p, kappa, medium, source); "
+                    f"oracle RHS build + GMRES(50) to 1e-6 per step, no preconditioner, setup excluded"}
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"bump_16cubed sampled at {args.cpu_sample_L}^3 leaves (CPU oracle)",
+                       "parallelism": "host cores"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            rec = run_reference(args, dist)
+        else:
+            rec = run_gpu(args, dist)
+            if rec is not None and dist.rank == 0 and dist.world == 1:
+                rec["cpu_baseline"] = cpu_baseline_record(args.cpu_sample_L)
+            elif rec is not None:
+                rec["cpu_baseline"] = None
+        if dist.rank == 0 and rec is not None:
+            print(json.dumps(rec), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,9 @@ extern "C" {
 /* Solve forms (bit flags for hps_options.forms). */
 #define HPS_FORM_FP64 1  /* everything in complex FP64 */
 #define HPS_FORM_MIXED 2 /* complex-FP32 apply/preconditioner inside FP64 Krylov + FP64 outer residual */
+/* OR'd into the form argument of hps_gmres_solve: run GMRES without the
+ * preconditioner even when it was built (the solution is the same). */
+#define HPS_SOLVE_NO_PRECOND 16
 
 typedef struct hps_handle hps_handle;
 
@@ -154,7 +157,8 @@ int hps_rhs(hps_handle* h, const double* s, const double* t, int nrhs, double* b
  * right-hand side, with the FP64 operator.  form: HPS_FORM_FP64 (restarted
  * GMRES in FP64) or HPS_FORM_MIXED (complex-FP32 apply and preconditioner
  * inside an FP64 Krylov basis, with the true residual recomputed in FP64 at
- * every restart, which restores FP64 accuracy).  s, t as in hps_rhs; f_out:
+ * every restart, which restores FP64 accuracy), optionally OR'd with
+ * HPS_SOLVE_NO_PRECOND.  s, t as in hps_rhs; f_out:
  * nrhs*N_f complex doubles.  Pointers may be host or device memory (detected
  * per pointer; host buffers are copied inside the call).  info may be NULL.
  * The call returns after the result is in f_out.
@@ -172,6 +176,30 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
  * Returns the number of doubles written (>0) or a negative error code;
  * with host_out == NULL only the size is returned. */
 long long hps_export(hps_handle* h, int what, int index, double* host_out);
+
+/* Phases timed by the profiler (indices into hps_profile.ms / count). */
+#define HPS_PHASE_APPLY 0     /* w = A z inside the Arnoldi loop (working precision) */
+#define HPS_PHASE_PRECOND_B 1 /* preconditioner stage B: z_ext = r_ext, t = r_int - B r_ext */
+#define HPS_PHASE_PRECOND_K 2 /* preconditioner stage K: z_int = K_c t */
+#define HPS_PHASE_ARNOLDI 3   /* CGS2 dots/updates, norm, Givens, scaling */
+#define HPS_PHASE_RESIDUAL 4  /* FP64 true residual b - A x at each restart */
+#define HPS_PHASE_RHS 5       /* right-hand side b = tbar - Pi H s */
+#define HPS_PHASE_UPDATE 6    /* least squares, x += M^{-1} V y */
+#define HPS_NPHASES 8
+
+typedef struct {
+  long long launches;        /* kernels launched by hps_gmres_solve / hps_apply / hps_precond */
+  double ms[HPS_NPHASES];    /* device time per phase (CUDA events on the call's stream) */
+  long long count[HPS_NPHASES]; /* timed intervals per phase */
+} hps_profile;
+
+/* Turns per-phase CUDA-event timing on (1) or off (0).  The launch counter
+ * always runs.  Timing adds two event records per timed interval. */
+int hps_profile_enable(hps_handle* h, int on);
+
+/* Copies the counters accumulated since the last reset into *out (waiting for
+ * the recorded events), and resets them when reset != 0. */
+int hps_profile_read(hps_handle* h, hps_profile* out, int reset);
 
 /* Device bytes held by the handle. */
 size_t hps_memory_bytes(const hps_handle* h);

@@ -127,7 +127,7 @@ class Solver:
         N.check(self.lib.hps_rhs(self.handle, _ptr(s), _ptr(t), nrhs, _ptr(out), _stream(stream)))
         return out
 
-    def solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=None, out=None, stream=None):
+    def solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=None, out=None, stream=None, precond=True):
         """Solve (I + Pi R) f = tbar - Pi H s.  s, t, out: torch tensors (device or host) or numpy
         arrays (host).  Returns (f, info dict)."""
         torch = _torch()
@@ -153,7 +153,8 @@ class Solver:
         t_keep, t_ptr = as_arg(t)
         o_keep, o_ptr = as_arg(out)
         info = N.SolveInfo()
-        rc = self.lib.hps_gmres_solve(self.handle, _FORMS[form], s_ptr, t_ptr, nrhs, float(tol), o_ptr,
+        code = _FORMS[form] | (0 if precond else N.HPS_SOLVE_NO_PRECOND)
+        rc = self.lib.hps_gmres_solve(self.handle, code, s_ptr, t_ptr, nrhs, float(tol), o_ptr,
                                       ctypes.byref(info), _stream(stream))
         if rc not in (N.HPS_OK, N.HPS_ENOCONV):
             N.check(rc)
@@ -169,6 +170,16 @@ class Solver:
         buf = np.zeros(n // 2, dtype=np.complex128)
         N.check(self.lib.hps_export(self.handle, codes[what], index, buf.ctypes.data_as(ctypes.c_void_p)))
         return buf
+
+    def profile(self, enable=None, reset=False):
+        """Per-phase device times (ms) and kernel launch count since the last reset."""
+        if enable is not None:
+            N.check(self.lib.hps_profile_enable(self.handle, 1 if enable else 0))
+        p = N.Profile()
+        N.check(self.lib.hps_profile_read(self.handle, ctypes.byref(p), 1 if reset else 0))
+        return {"launches": p.launches,
+                "ms": {name: p.ms[i] for i, name in enumerate(N.PHASES)},
+                "count": {name: p.count[i] for i, name in enumerate(N.PHASES)}}
 
     @property
     def memory_bytes(self):

@@ -17,6 +17,7 @@ HPS_C128 = 0
 HPS_C64 = 1
 HPS_FORM_FP64 = 1
 HPS_FORM_MIXED = 2
+HPS_SOLVE_NO_PRECOND = 16
 HPS_EXPORT_R = 0
 HPS_EXPORT_H = 1
 HPS_EXPORT_LAMBDA = 2
@@ -42,6 +43,12 @@ class SolveInfo(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double * 8), ("count", ctypes.c_longlong * 8)]
+
+
+PHASES = ["apply", "precond_b", "precond_k", "arnoldi", "residual", "rhs", "update"]
+
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 
@@ -57,6 +64,8 @@ SIGNATURES = {
                                        ctypes.POINTER(SolveInfo), _P]),
     "hps_export": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "hps_memory_bytes": (ctypes.c_size_t, [_P]),
+    "hps_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "hps_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile), ctypes.c_int]),
     "hps_destroy": (ctypes.c_int, [_P]),
     "hps_last_error": (ctypes.c_char_p, []),
 }

@@ -333,6 +333,8 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
     set_error("hps_gmres_solve: bad arguments");
     return HPS_EINVAL;
   }
+  const bool no_pc = (form & HPS_SOLVE_NO_PRECOND) != 0;
+  form &= ~HPS_SOLVE_NO_PRECOND;
   if (form != HPS_FORM_FP64 && form != HPS_FORM_MIXED) {
     set_error("hps_gmres_solve: form must be HPS_FORM_FP64 or HPS_FORM_MIXED");
     return HPS_EINVAL;
@@ -341,11 +343,11 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
     set_error("hps_gmres_solve: nrhs exceeds options.max_rhs");
     return HPS_EINVAL;
   }
-  if (form == HPS_FORM_MIXED && (!h->R32 || (h->has_precond && !h->Kc32))) {
+  if (form == HPS_FORM_MIXED && (!h->R32 || (h->has_precond && !no_pc && !h->Kc32))) {
     set_error("hps_gmres_solve: mixed-form operators were not built");
     return HPS_EINVAL;
   }
-  if (form == HPS_FORM_FP64 && h->has_precond && !h->Kc64) {
+  if (form == HPS_FORM_FP64 && h->has_precond && !no_pc && !h->Kc64) {
     set_error("hps_gmres_solve: FP64 preconditioner was not built");
     return HPS_EINVAL;
   }
@@ -369,10 +371,14 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
     HPS_CUDA_TRY(cudaMemcpyAsync(k.t_dev, t, (size_t)nrhs * h->nf * sizeof(double2), cudaMemcpyHostToDevice, st));
     td = k.t_dev;
   }
-  HPS_CUDA_TRY(launch_rhs(h, sd, td, k.b, nrhs, st));
+  {
+    cudaEvent_t ev = h->prof.begin(st);
+    HPS_CUDA_TRY(launch_rhs(h, sd, td, k.b, nrhs, st));
+    h->prof.end(HPS_PHASE_RHS, ev, st);
+  }
   const bool fdev = is_device_ptr(f_out);
   double2* x = fdev ? (double2*)f_out : k.x;
-  rc = gmres_solve(h, form, k.b, x, nrhs, tol, info, st);
+  rc = gmres_solve(h, form, k.b, x, nrhs, tol, info, st, !no_pc);
   if (rc != HPS_OK && rc != HPS_ENOCONV) return rc;
   if (!fdev) {
     HPS_CUDA_TRY(cudaMemcpyAsync(f_out, x, (size_t)nrhs * h->nf * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -446,6 +452,31 @@ long long hps_export(hps_handle* h, int what, int index, double* host_out) {
   }
   set_error("hps_export: bad 'what' or index");
   return HPS_EINVAL;
+}
+
+int hps_profile_enable(hps_handle* h, int on) {
+  if (!h) {
+    set_error("hps_profile_enable: NULL handle");
+    return HPS_EINVAL;
+  }
+  h->prof.on = on != 0;
+  return HPS_OK;
+}
+
+int hps_profile_read(hps_handle* h, hps_profile* out, int reset) {
+  if (!h || !out) {
+    set_error("hps_profile_read: bad arguments");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  h->prof.flush();
+  out->launches = h->prof.launches;
+  for (int i = 0; i < HPS_NPHASES; ++i) {
+    out->ms[i] = h->prof.ms[i];
+    out->count[i] = h->prof.count[i];
+  }
+  if (reset) h->prof.reset();
+  return HPS_OK;
 }
 
 size_t hps_memory_bytes(const hps_handle* h) { return h ? h->bytes + h->ks.bytes : 0; }

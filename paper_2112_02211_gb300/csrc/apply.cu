@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Ar
 }
 
 template <class P, int NR, int RPW>
-cudaError_t launch_one(const typename P::Args& A, int xcap, int q2, int nsm, cudaStream_t st) {
+cudaError_t launch_one(const typename P::Args& A, int xcap, int q2, int nsm, cudaStream_t st, long long* counter) {
   using Acc = typename P::Acc;
   const size_t smem = ((size_t)NR * xcap + (size_t)NR * q2) * sizeof(Acc);
   auto kern = seg_gemv_kernel<P, NR, RPW>;
@@ -353,22 +353,26 @@ cudaError_t launch_one(const typename P::Args& A, int xcap, int q2, int nsm, cud
   long long grid = std::min<long long>(A.nitems, (long long)nsm * occ);
   if (grid <= 0) return cudaSuccess;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(A, xcap);
+  ++*counter;
   return cudaGetLastError();
 }
 
 // Launch over right-hand-side groups of at most 8 (each group re-reads the matrix).
 template <class P, class Shift>
-cudaError_t launch_groups(typename P::Args A, int nrhs, int xcap, int q2, int nsm, cudaStream_t st, Shift shift) {
+cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int xcap, int q2, cudaStream_t st,
+                          Shift shift) {
+  const int nsm = h->nsm;
+  long long* counter = &h->prof.launches;
   for (int r0 = 0; r0 < nrhs; r0 += 8) {
     typename P::Args B = A;
     const int nr = std::min(8, nrhs - r0);
     shift(B, r0);
     B.nrhs = nr;
     cudaError_t e;
-    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, q2, nsm, st);
-    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, q2, nsm, st);
-    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, q2, nsm, st);
-    else e = launch_one<P, 8, 1>(B, xcap, q2, nsm, st);
+    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, q2, nsm, st, counter);
+    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, q2, nsm, st, counter);
+    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, q2, nsm, st, counter);
+    else e = launch_one<P, 8, 1>(B, xcap, q2, nsm, st, counter);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -398,7 +402,7 @@ cudaError_t apply_t(const hps_handle* h, const TM* R, const TIN* f, TOUT* y, con
   A.nf = h->nf;
   A.nrhs = nrhs;
   A.nitems = (long long)h->nl * 6;
-  return launch_groups<P>(A, nrhs, xcap_of(h), A.q2, h->nsm, st, [&](typename P::Args& B, int r0) {
+  return launch_groups<P>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename P::Args& B, int r0) {
     B.f += (long long)r0 * h->nf;
     B.y += (long long)r0 * h->nf;
     if (B.bvec) B.bvec += (long long)r0 * h->nf;
@@ -427,11 +431,13 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.tstride = tstride;
     A.nrhs = nrhs;
     A.nitems = (long long)h->nl * 6;
-    cudaError_t e = launch_groups<P>(A, nrhs, xcap_of(h), q2, h->nsm, st, [&](typename P::Args& X, int r0) {
+    cudaEvent_t ev = h->prof.begin(st);
+    cudaError_t e = launch_groups<P>(h, A, nrhs, xcap_of(h), q2, st, [&](typename P::Args& X, int r0) {
       X.r += (long long)r0 * h->nf;
       X.z += (long long)r0 * h->nf;
       X.t += (long long)r0 * tstride;
     });
+    h->prof.end(HPS_PHASE_PRECOND_B, ev, st);
     if (e != cudaSuccess) return e;
   }
   if (h->ct.nslots == 0) return cudaSuccess;
@@ -451,10 +457,13 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.tstride = tstride;
     A.nrhs = nrhs;
     A.nitems = h->ct.nslots;
-    return launch_groups<P>(A, nrhs, xcap_of(h), q2, h->nsm, st, [&](typename P::Args& X, int r0) {
+    cudaEvent_t ev = h->prof.begin(st);
+    cudaError_t e = launch_groups<P>(h, A, nrhs, xcap_of(h), q2, st, [&](typename P::Args& X, int r0) {
       X.t += (long long)r0 * tstride;
       X.z += (long long)r0 * h->nf;
     });
+    h->prof.end(HPS_PHASE_PRECOND_K, ev, st);
+    return e;
   }
 }
 
@@ -477,6 +486,14 @@ cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const
   return cudaErrorInvalidValue;
 }
 
+cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType tin, const void* f, VType tout,
+                        void* y, const double2* bvec, int nrhs, bool residual, cudaStream_t st) {
+  cudaEvent_t ev = h->prof.begin(st);
+  cudaError_t e = launch_apply(h, fp32_matrix, tin, f, tout, y, bvec, nrhs, residual, st);
+  h->prof.end(phase, ev, st);
+  return e;
+}
+
 cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
                        cudaStream_t st) {
   typename RhsP::Args A;
@@ -493,7 +510,7 @@ cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, 
   A.nint = h->nint;
   A.nrhs = nrhs;
   A.nitems = (long long)h->nl * 6;
-  return launch_groups<RhsP>(A, nrhs, xcap_of(h), A.q2, h->nsm, st, [&](typename RhsP::Args& B, int r0) {
+  return launch_groups<RhsP>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename RhsP::Args& B, int r0) {
     if (B.s) B.s += (long long)r0 * h->nint;
     if (B.t) B.t += (long long)r0 * h->nf;
     B.out += (long long)r0 * h->nf;

@@ -71,6 +71,68 @@ struct DeviceClusterTables {
   long long* b_off = nullptr;
 };
 
+// Per-phase CUDA-event timing and a launch counter (see hps_profile).
+struct Profiler {
+  bool on = false;
+  long long launches = 0;
+  double ms[HPS_NPHASES] = {};
+  long long count[HPS_NPHASES] = {};
+  struct Rec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> recs;
+  cudaEvent_t take() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  // Start of a timed interval on stream st (nullptr when timing is off).
+  cudaEvent_t begin(cudaStream_t st) {
+    if (!on) return nullptr;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, st);
+    return e;
+  }
+  void end(int phase, cudaEvent_t a, cudaStream_t st) {
+    if (!on || !a) return;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, st);
+    recs.push_back({phase, a, e});
+  }
+  void flush() {
+    for (const Rec& r : recs) {
+      cudaEventSynchronize(r.b);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.phase] += t;
+      count[r.phase] += 1;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  void reset() {
+    flush();
+    launches = 0;
+    for (int i = 0; i < HPS_NPHASES; ++i) {
+      ms[i] = 0;
+      count[i] = 0;
+    }
+  }
+  void destroy() {
+    flush();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 struct KrylovSpace {
   int m = 0, nrhs = 0, nblk = 0;
   long long nf = 0;
@@ -130,6 +192,7 @@ struct hps_handle {
   void* pc_scratch = nullptr;  // nslots*q^2*max_rhs complex double (precond t buffer)
 
   hps::KrylovSpace ks;
+  mutable hps::Profiler prof;
   size_t bytes = 0;
 };
 
@@ -155,11 +218,14 @@ cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, 
                        cudaStream_t st);
 cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, const void* r,
                            VType tout, void* z, void* scratch, int nrhs, cudaStream_t st);
+// Timed wrappers (phase intervals recorded when profiling is on).
+cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType tin, const void* f, VType tout,
+                        void* y, const double2* bvec, int nrhs, bool residual, cudaStream_t st);
 
 // ---- krylov.cu ----
 int krylov_alloc(hps_handle* h, int nrhs);
 void krylov_free(hps_handle* h);
 int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol,
-                hps_solve_info* info, cudaStream_t st);
+                hps_solve_info* info, cudaStream_t st, bool use_precond);
 
 }  // namespace hps

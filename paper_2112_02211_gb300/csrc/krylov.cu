@@ -398,6 +398,7 @@ int krylov_alloc(hps_handle* h, int nrhs) {
 }
 
 void krylov_free(hps_handle* h) {
+  h->prof.destroy();
   KrylovSpace& k = h->ks;
   void* ptrs[] = {k.V, k.x, k.r, k.b, k.u, k.z, k.zt, k.part, k.hcol, k.y, k.H, k.cs, k.sn, k.g, k.est, k.nrm, k.active,
                   k.s_dev, k.t_dev, k.f_dev};
@@ -417,6 +418,7 @@ int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& ou
   HPS_CUDA_TRY(cudaGetLastError());
   norm_final_kernel<<<(nrhs + 63) / 64, 64, 0, st>>>(part, nblk, nrhs, res);
   HPS_CUDA_TRY(cudaGetLastError());
+  h->prof.launches += 2;
   out.resize(nrhs);
   HPS_CUDA_TRY(cudaMemcpyAsync(out.data(), res, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   HPS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -426,7 +428,7 @@ int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& ou
 }  // namespace
 
 int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol, hps_solve_info* info,
-                cudaStream_t st) {
+                cudaStream_t st, bool use_precond) {
   const auto t0 = std::chrono::steady_clock::now();
   const bool mixed = (form == HPS_FORM_MIXED);
   int rc = krylov_alloc(h, nrhs);
@@ -455,7 +457,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
   std::vector<double> htarget(nrhs), hinv(nrhs);
   std::vector<int> hact(nrhs);
   bool converged = false;
-  const bool pc = h->has_precond;
+  const bool pc = h->has_precond && use_precond;
   while (true) {
     bool all = true;
     for (int r = 0; r < nrhs; ++r)
@@ -485,6 +487,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     }
     scale_copy_kernel<<<vgrid, 256, 0, st>>>(k.r, k.V, nf, invn);
     HPS_CUDA_TRY(cudaGetLastError());
+    h->prof.launches += 1;
     int jdone = 0;
     for (int j = 0; j < m && its < h->opt.maxit; ++j) {
       double2* vj = k.V + (long long)j * nrhs * nf;
@@ -493,16 +496,16 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       if (mixed) {
         if (pc) {
           HPS_CUDA_TRY(launch_precond(h, true, VType::C128, vj, VType::C64, k.z, k.zt, nrhs, st));
-          HPS_CUDA_TRY(launch_apply(h, true, VType::C64, k.z, VType::C128, w, nullptr, nrhs, false, st));
+          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::C64, k.z, VType::C128, w, nullptr, nrhs, false, st));
         } else {
-          HPS_CUDA_TRY(launch_apply(h, true, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
+          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
         }
       } else {
         if (pc) {
           HPS_CUDA_TRY(launch_precond(h, false, VType::C128, vj, VType::C128, k.z, k.zt, nrhs, st));
-          HPS_CUDA_TRY(launch_apply(h, false, VType::C128, k.z, VType::C128, w, nullptr, nrhs, false, st));
+          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, false, VType::C128, k.z, VType::C128, w, nullptr, nrhs, false, st));
         } else {
-          HPS_CUDA_TRY(launch_apply(h, false, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
+          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, false, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
         }
       }
       VecArgs va;
@@ -516,6 +519,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       va.part = k.part;
       va.active = active;
       const dim3 bgrid(k.nblk, nrhs);
+      cudaEvent_t ev_arn = h->prof.begin(st);
       mdot_kernel<<<bgrid, kT, 0, st>>>(va);
       HPS_CUDA_TRY(cudaGetLastError());
       reduce_kernel<<<nrhs, 64, 0, st>>>(k.part, k.nblk, j + 1, M1, k.hcol, M1 + 1, 0, active);
@@ -554,6 +558,8 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       HPS_CUDA_TRY(cudaGetLastError());
       scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);
       HPS_CUDA_TRY(cudaGetLastError());
+      h->prof.end(HPS_PHASE_ARNOLDI, ev_arn, st);
+      h->prof.launches += 7;
       ++its;
       jdone = j + 1;
       int hany = 0;
@@ -562,6 +568,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       if (!hany) break;
     }
     // x += M^{-1} (V y)
+    cudaEvent_t ev_up = h->prof.begin(st);
     lsq_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, m, M1, k.H, k.g, kcount, k.y);
     HPS_CUDA_TRY(cudaGetLastError());
     combine_kernel<<<vgrid, 256, 0, st>>>(k.V, nrhs, nf, jdone, m, k.y, k.u);
@@ -579,8 +586,10 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       xpy_kernel<double2><<<4 * h->nsm, 256, 0, st>>>(x, k.u, nall);
     }
     HPS_CUDA_TRY(cudaGetLastError());
+    h->prof.end(HPS_PHASE_UPDATE, ev_up, st);
+    h->prof.launches += 3;
     // true residual with the FP64 maps
-    HPS_CUDA_TRY(launch_apply(h, false, VType::C128, x, VType::C128, k.r, b, nrhs, true, st));
+    HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_RESIDUAL, false, VType::C128, x, VType::C128, k.r, b, nrhs, true, st));
     if ((rc = vec_norms(h, k.r, nrhs, rnorm, st))) return rc;
     ++cycles;
   }

@@ -10,6 +10,7 @@ class OracleCase:
     """Oracle maps, preconditioner and inputs of a workload (CPU, FP64)."""
 
     def __init__(self, w, with_precond=True, leaves=None):
+        # with_precond builds the oracle's cluster preconditioner (dense per-cluster solves)
         self.w = w
         self.grid = O.Grid(w.nx, w.ny, w.nz, w.p)
         g = self.grid
@@ -20,6 +21,7 @@ class OracleCase:
         self.s = w.sample_s(self.xi)
         self.t = w.sample_t(self.xf, self.nrm)
         self.prob = O.build_problem(g, w.kappa, w.eta, self.b, leaves=leaves)
+        self._cache = {}
         self.hom = None
         self.M = None
         if with_precond and leaves is None:
@@ -34,13 +36,19 @@ class OracleCase:
     def apply(self, f):
         return O.apply_face(self.grid, self.prob.R, f)
 
-    def solve(self, r=0, precond=True):
+    def solve(self, r=0):
+        """Oracle solution to round-off: dense LU on small grids, else GMRES to 1e-13
+        (unpreconditioned: the preconditioner never changes the solution)."""
+        key = ("solve", r)
+        if key in self._cache:
+            return self._cache[key]
         rhs = self.rhs(r)
         g = self.grid
         if g.nf <= 4000:
-            return np.linalg.solve(O.dense_face_matrix(g, self.prob.R), rhs)
-        f, its, hist = O.gmres(self.apply, rhs, tol=1e-13, restart=50,
-                               precond=self.M if precond else None)
+            f = np.linalg.solve(O.dense_face_matrix(g, self.prob.R), rhs)
+        else:
+            f, its, hist = O.gmres(self.apply, rhs, tol=1e-13, restart=50)
+        self._cache[key] = f
         return f
 
 

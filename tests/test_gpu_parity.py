@@ -156,7 +156,7 @@ def test_single_leaf_solution_is_boundary_data():
 @pytest.fixture(scope="module")
 def plane_wave_4cubed():
     w = W.plane_wave_4cubed()
-    oc = OracleCase(w)
+    oc = OracleCase(w, with_precond=False)
     xi, xf, b, s, t = gpu_inputs(w, hps)
     solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b)
     yield w, oc, solver, t
@@ -181,7 +181,7 @@ def test_plane_wave_4cubed_solve(plane_wave_4cubed, form, bar):
 @pytest.fixture(scope="module")
 def bump_4cubed():
     w = W.scaled(W.bump_16cubed(), 4)
-    oc = OracleCase(w)
+    oc = OracleCase(w, with_precond=False)
     xi, xf, b, s, t = gpu_inputs(w, hps)
     solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b)
     yield w, oc, solver, s
