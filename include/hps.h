@@ -144,6 +144,30 @@ int hps_apply(hps_handle* h, int dtype, const void* f, void* y, int nrhs, void* 
 int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream);
 
 /*
+ * The same preconditioner apply as hps_precond, for callers that must not
+ * have the library allocate device memory during the call: processes that
+ * hand the GPU's memory to their own pool at start-up, or that run inside a
+ * fixed budget they do not control, where a cudaMalloc from a library could
+ * fail, fragment the pool or stall the device.  (The paper has no
+ * counterpart; this is an interface convenience.)  The scratch for the
+ * cluster-internal right-hand sides lives in a static device array of
+ * HPS_PRECOND_NOALLOC_MAX_BYTES bytes compiled into the library, held on
+ * every device that loads it until the process exits.  A call needs
+ * (internal face slots) * q^2 * nrhs * sizeof(element) bytes of it (for the
+ * 16^3-leaf, p = 10 grid: 12.6 MB per complex-double right-hand side) and
+ * returns HPS_EINVAL with a message when that exceeds the array.  The first
+ * call on each device also looks up the array's device address (once per
+ * device); make that first call before any stream capture begins.  The array
+ * keeps whatever the last call left in it; nothing in it needs to start at
+ * zero, because every call overwrites the part it reads.  All calls share the one
+ * array: calls that may overlap on the GPU (other streams, other handles,
+ * other host threads) race on it and must be serialized by the caller.
+ * Arguments as in hps_precond.  Allocates no device memory.
+ */
+#define HPS_PRECOND_NOALLOC_MAX_BYTES ((size_t)16 << 20)
+int hps_precond_noalloc(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream);
+
+/*
  * Right-hand side of (*): b = tbar - Pi h with h^tau = H^tau s^tau.
  * s: nrhs interior vectors or NULL (s = 0); t: nrhs face vectors or NULL
  * (t = 0; only boundary-face entries are read).  s, t, b_out: device,

@@ -18,6 +18,7 @@ HPS_C64 = 1
 HPS_FORM_FP64 = 1
 HPS_FORM_MIXED = 2
 HPS_SOLVE_NO_PRECOND = 16
+HPS_PRECOND_NOALLOC_MAX_BYTES = 16 << 20
 HPS_EXPORT_R = 0
 HPS_EXPORT_H = 1
 HPS_EXPORT_LAMBDA = 2
@@ -59,6 +60,7 @@ SIGNATURES = {
                                  ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "hps_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_precond": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "hps_precond_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
     "hps_gmres_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P,
                                        ctypes.POINTER(SolveInfo), _P]),
