@@ -169,17 +169,26 @@ __global__ void __launch_bounds__(kT) axpy_kernel(VecArgs a, int mode) {
   }
 }
 
-// out[rhs][i] (=|+=) sum over blocks of part[rhs][blk][i], in block order.
-__global__ void reduce_kernel(const double2* part, int nblk, int nvec, int M1, double2* out, int ostride,
-                              int accumulate, const int* active) {
-  const int rhs = blockIdx.x;
+// out[rhs][i] (=|+=) sum over blocks of part[rhs][blk][i].  One CTA per
+// (i, rhs): thread t sums blocks t, t+256, ... in order, then a fixed shuffle
+// tree and a fixed sum over warps, so the result is the same on every run.
+__global__ void __launch_bounds__(kT) reduce_kernel(const double2* part, int nblk, int M1, double2* out, int ostride,
+                                                    int accumulate, const int* active) {
+  const int i = blockIdx.x, rhs = blockIdx.y;
   if (active && !active[rhs]) return;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double2 s = make_double2(0.0, 0.0);
-    const double2* p = part + (long long)rhs * nblk * M1 + i;
-    for (int b = 0; b < nblk; ++b) s = cadd(s, p[(long long)b * M1]);
+  const double2* p = part + (long long)rhs * nblk * M1 + i;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < nblk; b += kT) s = cadd(s, p[(long long)b * M1]);
+  s.x = warp_sum(s.x);
+  s.y = warp_sum(s.y);
+  __shared__ double2 red[kT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = red[0];
+    for (int w = 1; w < kT / 32; ++w) t = cadd(t, red[w]);
     double2* o = out + (long long)rhs * ostride + i;
-    *o = accumulate ? cadd(*o, s) : s;
+    *o = accumulate ? cadd(*o, t) : t;
   }
 }
 
@@ -207,8 +216,8 @@ __global__ void givens_kernel(GivensArgs a) {
   if (rhs >= a.nrhs) return;
   if (!a.active[rhs]) return;
   const int j = a.j;
-  double nrm2 = 0.0;
-  for (int b = 0; b < a.nblk; ++b) nrm2 += a.part[((long long)rhs * a.nblk + b) * a.M1].x;
+  // ||w||^2 was reduced into the spare last slot of hcol
+  const double nrm2 = a.hcol[(long long)rhs * (a.M1 + 1) + a.M1].x;
   const double hn = sqrt(nrm2);
   double2* Hc = a.H + (long long)rhs * a.M1 * a.m;  // Hc[i*m + j]
   for (int i = 0; i <= j; ++i) Hc[i * a.m + j] = cadd(a.hcol[(long long)rhs * (a.M1 + 1) + i], a.h2[(long long)rhs * a.M1 + i]);
@@ -522,17 +531,19 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       cudaEvent_t ev_arn = h->prof.begin(st);
       mdot_kernel<<<bgrid, kT, 0, st>>>(va);
       HPS_CUDA_TRY(cudaGetLastError());
-      reduce_kernel<<<nrhs, 64, 0, st>>>(k.part, k.nblk, j + 1, M1, k.hcol, M1 + 1, 0, active);
+      reduce_kernel<<<dim3(j + 1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, k.hcol, M1 + 1, 0, active);
       HPS_CUDA_TRY(cudaGetLastError());
       va.coef = k.hcol;
       va.cstride = M1 + 1;
       axpy_kernel<<<bgrid, kT, 0, st>>>(va, 1);
       HPS_CUDA_TRY(cudaGetLastError());
-      reduce_kernel<<<nrhs, 64, 0, st>>>(k.part, k.nblk, j + 1, M1, h2, M1, 0, active);
+      reduce_kernel<<<dim3(j + 1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, h2, M1, 0, active);
       HPS_CUDA_TRY(cudaGetLastError());
       va.coef = h2;
       va.cstride = M1;
       axpy_kernel<<<bgrid, kT, 0, st>>>(va, 2);
+      HPS_CUDA_TRY(cudaGetLastError());
+      reduce_kernel<<<dim3(1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, k.hcol + M1, M1 + 1, 0, active);
       HPS_CUDA_TRY(cudaGetLastError());
       HPS_CUDA_TRY(cudaMemsetAsync(any_active, 0, sizeof(int), st));
       GivensArgs ga;
@@ -559,7 +570,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);
       HPS_CUDA_TRY(cudaGetLastError());
       h->prof.end(HPS_PHASE_ARNOLDI, ev_arn, st);
-      h->prof.launches += 7;
+      h->prof.launches += 8;
       ++its;
       jdone = j + 1;
       int hany = 0;
