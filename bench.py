@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--L", type=int, default=16, help="leaves per axis (16 = the benchmark workload)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / no-preconditioner comparison runs")
     ap.add_argument("--cpu-sample-L", type=int, default=4)
+    ap.add_argument("--serving-requests", type=int, default=16,
+                    help="requests of the scaled serving stream timed after the solves (0 = skip)")
     return ap.parse_args()
 
 
@@ -164,14 +166,16 @@ def apply_bytes(L, q, mat_bytes, in_bytes, out_bytes):
     return interior_face_pairs(L) * q * q * nb * mat_bytes + nf * (2 * in_bytes + out_bytes)
 
 
-def precond_bytes(L, q, mat_bytes, vec_bytes):
-    """Stage K: K_c of every 2x2x2 cluster + t read + z_int write; stage B: B blocks + r + t + z_ext."""
+def precond_bytes(L, q, mat_bytes, vec_bytes, in_bytes=None, scale_bytes=0):
+    """Stage K: K_c of every 2x2x2 cluster (+ one row scale for FP16 blocks) + t read + z_int
+    write.  Stage B: B blocks (+ row scales) + r read once + t and z_ext written."""
+    in_bytes = vec_bytes if in_bytes is None else in_bytes
     q2 = q * q
     ncl = (L // 2) ** 3
     nint = 24 * q2
-    kb = ncl * nint * nint * mat_bytes + ncl * nint * 2 * vec_bytes
+    kb = ncl * nint * (nint * mat_bytes + scale_bytes) + ncl * nint * 2 * vec_bytes
     nf = L ** 3 * 6 * q2
-    bb = L ** 3 * (3 * q2) * (3 * q2) * mat_bytes + nf * 3 * vec_bytes
+    bb = L ** 3 * (3 * q2) * (3 * q2 * mat_bytes + scale_bytes) + nf * in_bytes + nf * vec_bytes
     return kb, bb
 
 
@@ -285,12 +289,15 @@ def run_gpu(args, dist):
     # roofline of the dominant kernel and of the ItI apply, from the library's events
     pk, pk_src = peaks()
     q2 = q * q
-    a_bytes = apply_bytes(L, q, 8, 8, 16)  # c64 maps, c64 input, c128 output
-    kb, bb = precond_bytes(L, q, 8, 8)
+    # c64 maps, c64 input, double-float (16-byte) output
+    a_bytes = apply_bytes(L, q, 8, 8, 16)
+    # FP16 blocks (4 bytes per complex entry + a 4-byte scale per row), c64 vectors,
+    # double-float (16-byte) input to stage B
+    kb, bb = precond_bytes(L, q, 4, 8, in_bytes=16, scale_bytes=4)
     phases = {"apply": a_bytes, "precond_k": kb, "precond_b": bb}
-    kernels = {"apply": "seg_gemv_kernel<ApplyP<float2,float2,double2>,1,4>",
-               "precond_k": "seg_gemv_kernel<PrecKP<float2,float2,float2>,1,4>",
-               "precond_b": "seg_gemv_kernel<PrecBP<float2,double2,float2>,1,4>"}
+    kernels = {"apply": "seg_gemv_kernel<ApplyP<float2,float2,float4>,1,4>",
+               "precond_k": "seg_gemv_kernel<PrecKP<__half2,float2,float2>,1,4>",
+               "precond_b": "seg_gemv_kernel<PrecBP<__half2,float4,float2>,1,4>"}
     roof = {}
     for ph, by in phases.items():
         cnt = prof["count"][ph]
@@ -314,13 +321,14 @@ def run_gpu(args, dist):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64 operators, f64 Krylov/residual",
+        "dtype": "c64 operators, double-float Krylov, f64 residual",
         "data": "synthetic",
         "config": {
             "workload": f"bump_{L}cubed: {L}^3 leaves, p={p}, q={q}, kappa=eta={w.kappa:g}, "
                         f"b=1.5exp(-160|x-c|^2), s=exp(-400|x-x0|^2), t=0, tol={w.tol:g}",
-            "form": "mixed (complex-FP32 apply/precond, FP64 CGS2 Arnoldi, FP64 restart residual)",
-            "preconditioner": "2x2x2 cluster block Jacobi, homogenized leaf maps",
+            "form": "mixed (complex-FP32 apply and preconditioner, CGS2 Arnoldi in double-float "
+                    "(FP64-accurate, FP32 pipe), FP64 restart residual)",
+            "preconditioner": "2x2x2 cluster block Jacobi, homogenized leaf maps, blocks in FP16 with FP32 row scales",
             "restart": 50,
             "face_unknowns": nf,
             "paper_unknowns": L ** 3 * ((p - 2) ** 3 + 6 * (p - 2) ** 2),
@@ -343,7 +351,28 @@ def run_gpu(args, dist):
         "compare": compare,
     }
     solver.close()
+    if args.serving_requests > 0:
+        rec["serving"] = run_serving(args, dist)
     return rec
+
+
+def run_serving(args, dist):
+    """A bounded, scaled sample of the serving stream: Poisson arrivals at 20/s, grids of
+    4^3-8^3 leaves, p in {8, 10}, kappa in [20, 60], 3-8 bumps, 1-16 sources; mixed form,
+    tol 1e-6, admission by an HBM budget of 64 GiB, up to 4 requests in flight.
+    Latency = arrival to result on the host, including setup."""
+    from paper_2112_02211_gb300.serving import HPSBackend, Request, Server, latency_stats
+
+    ws = W.serving_stream(n=args.serving_requests, rate=20.0, seed=7, L_range=(4, 8), p_choices=(8, 10),
+                          kappa_range=(20.0, 60.0), max_sources=16)
+    reqs = [Request(i, w, w.meta["arrival"]) for i, w in enumerate(ws)]
+    srv = Server(HPSBackend(form="mixed", device=dist.local), hbm_budget=64 << 30, max_active=4)
+    res = srv.run(reqs)
+    st = latency_stats(res)
+    st.update({"requests": len(reqs), "peak_active": srv.peak_active, "peak_budget_bytes": srv.peak_bytes,
+               "stream": "serving recipe scaled to 4^3-8^3 leaves, p in {8,10}, kappa in [20,60]; "
+                         "latency includes per-request setup"})
+    return st
 
 
 # --------------------------------------------------------------------------------------------

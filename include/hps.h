@@ -61,6 +61,9 @@ extern "C" {
 /* Element types of device vectors passed to hps_apply / hps_precond. */
 #define HPS_C128 0 /* complex double, 16 bytes */
 #define HPS_C64 1  /* complex float, 8 bytes */
+/* hps_precond only: complex float vectors, preconditioner blocks read from their
+ * FP16 copies (one FP32 scale per row), as the mixed-form solve does. */
+#define HPS_C64_H16 2
 
 /* Solve forms (bit flags for hps_options.forms). */
 #define HPS_FORM_FP64 1  /* everything in complex FP64 */
@@ -86,6 +89,10 @@ typedef struct {
   int max_rhs;        /* maximum right-hand sides per solve (default 1) */
   size_t hbm_budget;  /* bytes the handle may allocate; 0 = no limit */
   int device;         /* CUDA device ordinal */
+  int precond_fp16;   /* mixed form: also keep the preconditioner blocks in FP16 with one FP32
+                         scale per row and use them in hps_gmres_solve (default 1) */
+  int tc_apply;       /* complex-FP32 apply of 64, 128, ... right-hand sides on the tensor cores
+                         (three TF32 products, FP32 accumulation; default 1) */
 } hps_options;
 
 typedef struct {
@@ -124,6 +131,15 @@ int hps_nodes(const hps_grid* grid, double* interior_xyz, double* face_xyz);
  */
 int hps_setup(const hps_grid* grid, double kappa, double eta, const double* b,
               const hps_options* opt, hps_handle** out);
+
+/*
+ * Device bytes that hps_setup with these options would hold, plus the Krylov
+ * workspace of one hps_gmres_solve with nrhs right-hand sides given as host
+ * buffers, plus the largest transient setup workspace (taken at most
+ * min(opt->hbm_budget, 24 GiB) when a budget is set).  For admission control
+ * by an HBM budget.  Returns 0 for an invalid grid or options.  No device work.
+ */
+size_t hps_setup_bytes(const hps_grid* grid, const hps_options* opt, int nrhs);
 
 /*
  * y = (I + Pi R) f for nrhs right-hand sides (the operator of (*); Sec. 2.2,
@@ -189,6 +205,17 @@ int hps_rhs(hps_handle* h, const double* s, const double* t, int nrhs, double* b
  */
 int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs,
                     double tol, double* f_out, hps_solve_info* info, void* stream);
+
+/*
+ * Leaf solutions at the interior nodes from face data (eq. (leaf)):
+ * u^tau = A^{tau,-1} [s^tau; P^{-1} f^tau], P^{-1} moving the Gauss-point face
+ * data to the leaf's Chebyshev face nodes.  s: nrhs interior vectors or NULL
+ * (s = 0); f: nrhs face vectors (typically the output of hps_gmres_solve);
+ * u_out: nrhs interior vectors (layout of hps_nodes' interior points).  All
+ * device pointers, complex double; one FP64 elimination per leaf and call
+ * (cost comparable to hps_setup's).  Synchronous.
+ */
+int hps_recover(hps_handle* h, const double* s, const double* f, int nrhs, double* u_out, void* stream);
 
 /* What hps_export copies out (host doubles, interleaved complex). */
 #define HPS_EXPORT_R 0      /* R^index, 6q^2 x 6q^2 row-major, FP64 */

@@ -66,7 +66,7 @@ class Solver:
     """One medium on one grid: leaf ItI maps, preconditioner and Krylov workspace on the GPU."""
 
     def __init__(self, nx, ny, nz, p, kappa, eta=None, b=None, forms=("fp64", "mixed"), restart=50,
-                 cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0):
+                 cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0, precond_fp16=True, tc_apply=True):
         self.lib = N.load()
         self.nx, self.ny, self.nz, self.p, self.q = nx, ny, nz, p, p - 2
         self.nl = nx * ny * nz
@@ -86,6 +86,8 @@ class Solver:
         opt.max_rhs = max_rhs
         opt.hbm_budget = hbm_budget
         opt.device = device
+        opt.precond_fp16 = 1 if precond_fp16 else 0
+        opt.tc_apply = 1 if tc_apply else 0
         bb = None
         if b is not None:
             bb = np.ascontiguousarray(np.asarray(b, dtype=np.complex128).reshape(-1))
@@ -112,10 +114,11 @@ class Solver:
         N.check(self.lib.hps_apply(self.handle, dt, _ptr(f), _ptr(y), self._nrhs(f), _stream(stream)))
         return y
 
-    def precond(self, r, out=None, stream=None):
-        """z = J^{-1} r (cluster block Jacobi with homogenized leaf maps)."""
+    def precond(self, r, out=None, stream=None, fp16_blocks=False):
+        """z = J^{-1} r (cluster block Jacobi with homogenized leaf maps).  complex64 input
+        reads the FP32 blocks, or their FP16 copies with fp16_blocks=True."""
         torch = _torch()
-        dt = N.HPS_C128 if r.dtype == torch.complex128 else N.HPS_C64
+        dt = N.HPS_C128 if r.dtype == torch.complex128 else (N.HPS_C64_H16 if fp16_blocks else N.HPS_C64)
         z = torch.empty_like(r) if out is None else out
         N.check(self.lib.hps_precond(self.handle, dt, _ptr(r), _ptr(z), self._nrhs(r), _stream(stream)))
         return z
@@ -161,6 +164,14 @@ class Solver:
         d = {"iterations": info.iterations, "cycles": info.cycles, "converged": bool(info.converged),
              "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc}
         return out, d
+
+    def recover(self, f, s=None, nrhs=None, stream=None):
+        """Leaf solutions at the interior nodes, u = A^{-1}[s; P^{-1} f] per leaf (device tensors)."""
+        torch = _torch()
+        nrhs = nrhs or self._nrhs(f)
+        u = torch.empty(nrhs * self.nl * self.ni, dtype=torch.complex128, device="cuda")
+        N.check(self.lib.hps_recover(self.handle, _ptr(s), _ptr(f), nrhs, _ptr(u), _stream(stream)))
+        return u
 
     def export(self, what, index):
         """Copy one stored operator block to the host (numpy complex128)."""

@@ -15,6 +15,7 @@ HPS_EBREAKDOWN = -5
 HPS_ETIMEOUT = -6
 HPS_C128 = 0
 HPS_C64 = 1
+HPS_C64_H16 = 2
 HPS_FORM_FP64 = 1
 HPS_FORM_MIXED = 2
 HPS_SOLVE_NO_PRECOND = 16
@@ -36,7 +37,7 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("forms", ctypes.c_int), ("restart", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("max_rhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("precond_fp16", ctypes.c_int), ("tc_apply", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -64,8 +65,10 @@ SIGNATURES = {
     "hps_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
     "hps_gmres_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P,
                                        ctypes.POINTER(SolveInfo), _P]),
+    "hps_recover": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
     "hps_export": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "hps_memory_bytes": (ctypes.c_size_t, [_P]),
+    "hps_setup_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), ctypes.POINTER(Options), ctypes.c_int]),
     "hps_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "hps_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile), ctypes.c_int]),
     "hps_destroy": (ctypes.c_int, [_P]),

@@ -1,6 +1,7 @@
 // C ABI of the HPS library (declared in include/hps.h).  Argument checks,
 // allocation of the handle's device state, and dispatch to the kernels of
 // setup.cu, apply.cu and krylov.cu.  Nothing here throws across the ABI.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -82,12 +83,54 @@ void free_handle(hps_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   krylov_free(h);
   void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->lambda, h->Kc64, h->Kc32, h->B64, h->B32, h->pc_scratch,
+                  h->Kc16, h->Kc16s, h->B16, h->B16s, h->tc_error, h->cdiag,
                   h->dct.slot_lf, h->dct.slot_cluster, h->dct.cl_slot_begin, h->dct.cl_kc_off, h->dct.lf_slot,
                   h->dct.int_mask, h->dct.b_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+void init_fields(hps_handle* h, const hps_grid* g, double kappa, double eta, const hps_options& o) {
+  h->opt = o;
+  h->dev = o.device;
+  h->nx = g->nx;
+  h->ny = g->ny;
+  h->nz = g->nz;
+  h->p = g->p;
+  h->q = g->q;
+  h->n1 = g->p - 2;
+  h->ni = h->n1 * h->n1 * h->n1;
+  h->nb = 6 * h->q * h->q;
+  h->n = h->ni + h->nb;
+  h->nl = g->nx * g->ny * g->nz;
+  h->nf = (long long)h->nl * h->nb;
+  h->nint = (long long)h->nl * h->ni;
+  h->kappa = kappa;
+  h->eta = eta;
+  h->h[0] = 1.0 / g->nx;
+  h->h[1] = 1.0 / g->ny;
+  h->h[2] = 1.0 / g->nz;
+  h->tl = TableLayout(g->p);
+  h->ldR = (int)rup4(h->nb);
+  h->ldH = (int)rup4(h->ni);
+}
+
+int check_options(const hps_options& o) {
+  if (o.restart < 1 || o.restart > 60) {
+    set_error("restart must be in 1..60");
+    return HPS_EINVAL;
+  }
+  if (o.cluster != 0 && o.cluster != 2) {
+    set_error("cluster must be 0 (no preconditioner) or 2");
+    return HPS_EINVAL;
+  }
+  if (o.max_rhs < 1 || o.max_rhs > 1024 || o.maxit < 1 || !(o.forms & (HPS_FORM_FP64 | HPS_FORM_MIXED))) {
+    set_error("bad options (max_rhs, maxit or forms)");
+    return HPS_EINVAL;
+  }
+  return HPS_OK;
 }
 
 int check_finite(const double* v, long long n, const char* what) {
@@ -112,6 +155,8 @@ void hps_default_options(hps_options* o) {
   o->max_rhs = 1;
   o->hbm_budget = 0;
   o->device = 0;
+  o->precond_fp16 = 1;
+  o->tc_apply = 1;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -159,41 +204,9 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
   hps_options o;
   hps_default_options(&o);
   if (opt) o = *opt;
-  if (o.restart < 1 || o.restart > 60) {
-    set_error("restart must be in 1..60");
-    return HPS_EINVAL;
-  }
-  if (o.cluster != 0 && o.cluster != 2) {
-    set_error("cluster must be 0 (no preconditioner) or 2");
-    return HPS_EINVAL;
-  }
-  if (o.max_rhs < 1 || o.max_rhs > 1024 || o.maxit < 1 || !(o.forms & (HPS_FORM_FP64 | HPS_FORM_MIXED))) {
-    set_error("bad options (max_rhs, maxit or forms)");
-    return HPS_EINVAL;
-  }
+  if ((rc = check_options(o))) return rc;
   hps_handle* h = new hps_handle();
-  h->opt = o;
-  h->dev = o.device;
-  h->nx = g->nx;
-  h->ny = g->ny;
-  h->nz = g->nz;
-  h->p = g->p;
-  h->q = g->q;
-  h->n1 = g->p - 2;
-  h->ni = h->n1 * h->n1 * h->n1;
-  h->nb = 6 * h->q * h->q;
-  h->n = h->ni + h->nb;
-  h->nl = g->nx * g->ny * g->nz;
-  h->nf = (long long)h->nl * h->nb;
-  h->nint = (long long)h->nl * h->ni;
-  h->kappa = kappa;
-  h->eta = eta;
-  h->h[0] = 1.0 / g->nx;
-  h->h[1] = 1.0 / g->ny;
-  h->h[2] = 1.0 / g->nz;
-  h->tl = TableLayout(g->p);
-  h->ldR = (int)rup4(h->nb);
-  h->ldH = (int)rup4(h->ni);
+  init_fields(h, g, kappa, eta, o);
   if (b && (rc = check_finite(b, 2 * h->nint, "b"))) {
     delete h;
     return rc;
@@ -213,11 +226,14 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
     if (want32 && (r = dalloc(h, (void**)&h->R32, rel * sizeof(float2)))) return r;
     if ((r = dalloc(h, (void**)&h->H64, (size_t)h->nl * h->nb * h->ldH * sizeof(double2)))) return r;
     if ((r = dalloc(h, (void**)&h->lambda, (size_t)h->nl * sizeof(double2)))) return r;
+    if ((r = dalloc(h, (void**)&h->tc_error, sizeof(int)))) return r;
+    HPS_CUDA_TRY(cudaMemsetAsync(h->tc_error, 0, sizeof(int), st));
     HPS_CUDA_TRY(cudaMemsetAsync(h->R64, 0, rel * sizeof(double2), st));
     if (h->R32) HPS_CUDA_TRY(cudaMemsetAsync(h->R32, 0, rel * sizeof(float2), st));
     HPS_CUDA_TRY(cudaMemsetAsync(h->H64, 0, (size_t)h->nl * h->nb * h->ldH * sizeof(double2), st));
     HPS_CUDA_TRY(cudaMalloc(&db, (size_t)h->nint * sizeof(double2)));
-    HPS_CUDA_TRY(cudaMalloc(&dc, (size_t)h->nint * sizeof(double2)));
+    if ((r = dalloc(h, (void**)&h->cdiag, (size_t)h->nint * sizeof(double2)))) return r;
+    dc = h->cdiag;
     if (b)
       HPS_CUDA_TRY(cudaMemcpyAsync(db, b, (size_t)h->nint * sizeof(double2), cudaMemcpyHostToDevice, st));
     else
@@ -244,19 +260,77 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
       const size_t ts = std::max<size_t>(1, (size_t)ct.nslots * h->q * h->q) * o.max_rhs * sizeof(double2);
       if ((r = dalloc(h, &h->pc_scratch, ts))) return r;
       if ((r = build_preconditioner(h, dc, st))) return r;
+      if (want32 && o.precond_fp16) {
+        const int q2 = h->q * h->q;
+        const size_t ke = std::max<long long>(1, ct.kc_elems), be = std::max<long long>(1, ct.b_elems);
+        if ((r = dalloc(h, (void**)&h->Kc16, ke * sizeof(__half2)))) return r;
+        if ((r = dalloc(h, (void**)&h->B16, be * sizeof(__half2)))) return r;
+        if ((r = dalloc(h, (void**)&h->Kc16s, std::max<size_t>(1, (size_t)ct.nslots * q2) * sizeof(float)))) return r;
+        if ((r = dalloc(h, (void**)&h->B16s, (size_t)h->nl * 6 * q2 * sizeof(float)))) return r;
+        HPS_CUDA_TRY(cudaMemsetAsync(h->Kc16, 0, ke * sizeof(__half2), st));
+        HPS_CUDA_TRY(cudaMemsetAsync(h->B16, 0, be * sizeof(__half2), st));
+        if ((r = build_precond_fp16(h, st))) return r;
+      }
     }
     HPS_CUDA_TRY(cudaStreamSynchronize(st));
     return HPS_OK;
   };
   rc = body();
   if (db) cudaFree(db);
-  if (dc) cudaFree(dc);
   if (rc) {
     free_handle(h);
     return rc;
   }
   *out = h;
   return HPS_OK;
+}
+
+size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
+  if (validate_grid(g)) return 0;
+  hps_options o;
+  hps_default_options(&o);
+  if (opt) o = *opt;
+  if (check_options(o) || nrhs < 1) return 0;
+  hps_handle h;
+  init_fields(&h, g, 1.0, 1.0, o);
+  if (cudaDeviceGetAttribute(&h.nsm, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess) {
+    cudaGetLastError();
+    h.nsm = 152;
+  }
+  const bool want64 = (o.forms & HPS_FORM_FP64) != 0, want32 = (o.forms & HPS_FORM_MIXED) != 0;
+  const size_t c16 = sizeof(double2), c8 = sizeof(float2);
+  const size_t rel = (size_t)h.nl * h.nb * h.ldR;
+  size_t bytes = h.tl.total * sizeof(double) + rel * c16 + (want32 ? rel * c8 : 0) +
+                 (size_t)h.nl * h.nb * h.ldH * c16 + (size_t)h.nl * c16;
+  const int q2 = h.q * h.q;
+  size_t nslots = 0;
+  if (o.cluster == 2) {
+    build_cluster_tables(&h, 2);
+    const ClusterTables& ct = h.ct;
+    nslots = ct.nslots;
+    bytes += 2 * ct.slot_lf.size() * sizeof(int) + ct.cl_slot_begin.size() * sizeof(int) +
+             ct.cl_kc_off.size() * sizeof(long long) + ct.lf_slot.size() * sizeof(int) + ct.int_mask.size() +
+             ct.b_off.size() * sizeof(long long);
+    if (want64) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c16;
+    if (want32) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c8;
+    if (want32 && o.precond_fp16)
+      bytes += (size_t)(ct.kc_elems + ct.b_elems) * sizeof(__half2) + nslots * q2 * sizeof(float) +
+               (size_t)h.nl * 6 * q2 * sizeof(float);
+    bytes += std::max<size_t>(1, nslots * q2) * o.max_rhs * c16;
+  }
+  bytes += (size_t)h.nint * c16 + sizeof(int);  // medium C kept for recovery, error word
+  // Krylov workspace of one solve (host inputs staged on the device)
+  const int M1 = o.restart + 1;
+  const size_t vb = (size_t)nrhs * h.nf * c16;
+  const long long nblk = (h.nf + 511) / 512;
+  bytes += vb * (M1 + 5) + std::max<size_t>(1, nslots * q2) * nrhs * c16 + (size_t)nrhs * nblk * M1 * c16 +
+           (size_t)o.max_rhs * (h.nint + h.nf) * c16 + (size_t)nrhs * (3 * M1 + 4 * o.restart + 8) * c16 +
+           (size_t)nrhs * std::max<long long>(256, nblk) * sizeof(double);
+  // transient setup workspace (largest phase) + medium staging
+  const size_t cap = workspace_cap(&h);
+  size_t trans = exact_maps_workspace(&h, cap, nullptr);
+  if (o.cluster == 2) trans = std::max(trans, precond_workspace(&h, cap, nullptr));
+  return bytes + trans + (size_t)h.nint * c16;
 }
 
 int hps_apply(hps_handle* h, int dtype, const void* f, void* y, int nrhs, void* stream) {
@@ -293,7 +367,7 @@ int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void
   HPS_CUDA_TRY(cudaSetDevice(h->dev));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = (dtype == HPS_C128) ? sizeof(double2) : sizeof(float2);
-  if (dtype != HPS_C128 && dtype != HPS_C64) {
+  if (dtype != HPS_C128 && dtype != HPS_C64 && dtype != HPS_C64_H16) {
     set_error("hps_precond: unknown dtype");
     return HPS_EINVAL;
   }
@@ -307,6 +381,12 @@ int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void
       return HPS_EINVAL;
     }
     HPS_CUDA_TRY(launch_precond(h, false, VType::C128, r, VType::C128, z, h->pc_scratch, nrhs, st));
+  } else if (dtype == HPS_C64_H16) {
+    if (!h->Kc16) {
+      set_error("hps_precond: FP16 preconditioner blocks were not built (options.precond_fp16)");
+      return HPS_EINVAL;
+    }
+    HPS_CUDA_TRY(launch_precond(h, true, VType::C64, r, VType::C64, z, h->pc_scratch, nrhs, st, true));
   } else {
     if (!h->Kc32) {
       set_error("hps_precond: FP32 preconditioner was not built (HPS_FORM_MIXED)");
@@ -386,6 +466,15 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
   HPS_CUDA_TRY(cudaStreamSynchronize(st));
   if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return rc;
+}
+
+int hps_recover(hps_handle* h, const double* s, const double* f, int nrhs, double* u_out, void* stream) {
+  if (!h || !f || !u_out || nrhs < 1 || nrhs > 1024) {
+    set_error("hps_recover: bad arguments");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  return recover_interior(h, (const double2*)s, (const double2*)f, nrhs, (double2*)u_out, (cudaStream_t)stream);
 }
 
 long long hps_export(hps_handle* h, int what, int index, double* host_out) {

@@ -29,6 +29,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+// One 16-byte load per lane: VPL complex entries of the matrix type, widened to
+// the accumulation type.
 template <class TM> struct MT;
 template <> struct MT<double2> {
   static constexpr int VPL = 1;
@@ -44,6 +46,23 @@ template <> struct MT<float2> {
     v[1] = make_float2(t.z, t.w);
   }
 };
+template <> struct MT<__half2> {
+  static constexpr int VPL = 4;
+  using Acc = float2;
+  __device__ static __forceinline__ void load(const __half2* p, float2 (&v)[4]) {
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+    v[0] = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
+    v[1] = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
+    v[2] = __half22float2(*reinterpret_cast<const __half2*>(&t.z));
+    v[3] = __half22float2(*reinterpret_cast<const __half2*>(&t.w));
+  }
+};
+__device__ __forceinline__ float2 rscale(float2 v, const float* s, long long i) {
+  if (!s) return v;
+  const float f = s[i];
+  return make_float2(v.x * f, v.y * f);
+}
+__device__ __forceinline__ double2 rscale(double2 v, const float*, long long) { return v; }
 
 struct ItemInfo {
   const void* mat;
@@ -51,9 +70,33 @@ struct ItemInfo {
   long long ooff;  // base offset of the output (per rhs)
   long long aoff;  // auxiliary offset (neighbour input / residual base)
   int ld, ncols;
+  int nrows;       // matrix rows of the item (q^2, or all internal-face rows of a leaf)
   int leaf, face, nbr;
   int mask;        // precond B: internal-face mask of the leaf
 };
+
+// ---------------------------------------------------------------------------
+// y = f + g (apply) in the output's precision.  Double-float outputs (float4)
+// keep f + g exactly (TwoSum), so the identity part of I + Pi R loses nothing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sum_out(double2& y, double2 f, double2 g) { y = cadd(f, g); }
+__device__ __forceinline__ void sum_out(double2& y, float2 f, float2 g) {
+  y = make_double2((double)f.x + (double)g.x, (double)f.y + (double)g.y);
+}
+__device__ __forceinline__ void sum_out(double2& y, double2 f, float2 g) {
+  y = make_double2(f.x + (double)g.x, f.y + (double)g.y);
+}
+__device__ __forceinline__ void sum_out(float2& y, float2 f, float2 g) { y = cadd(f, g); }
+__device__ __forceinline__ void sum_out(float4& y, float2 f, float2 g) {
+  const dfr re = df_two_sum(f.x, g.x), im = df_two_sum(f.y, g.y);
+  y = make_float4(re.h, im.h, re.l, im.l);
+}
+__device__ __forceinline__ void sum_out(float4& y, float4 f, float2 g) {
+  y = dfc_store(dfc_add(dfc_load(f), dfc{{g.x, 0.f}, {g.y, 0.f}}));
+}
+// residual form y = b - (f + g): only produced in complex double
+__device__ __forceinline__ void residual_out(double2& y, double2 b) { y = csub(b, y); }
+template <class T> __device__ __forceinline__ void residual_out(T&, double2) {}
 
 // ---------------------------------------------------------------------------
 // Policies
@@ -85,27 +128,29 @@ struct ApplyP {
     it.mat = A.R + (long long)it.leaf * A.nb * A.ldR + (long long)it.face * A.q2 * A.ldR;
     it.ld = A.ldR;
     it.ncols = A.nb;
+    it.nrows = A.q2;
     it.ooff = (long long)it.nbr * A.nb + (long long)(it.face ^ 1) * A.q2;
     return true;
   }
   __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
     return cvt<Acc>(A.f[rhs * A.nf + it.xoff + c]);
   }
-  __device__ static void finish(const Args& A, long long o, double2 g) {
-    double2 v = cadd(cvt<double2>(A.f[o]), g);
-    if (A.bvec) v = csub(A.bvec[o], v);
-    A.y[o] = cvt<TOUT>(v);
+  __device__ static void finish(const Args& A, long long o, Acc g) {
+    TOUT v;
+    sum_out(v, A.f[o], g);
+    if (A.bvec) residual_out(v, A.bvec[o]);
+    A.y[o] = v;
   }
   __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
     for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
       const int rhs = idx / A.q2, j = idx % A.q2;
-      finish(A, rhs * A.nf + it.ooff + j, cvt<double2>(outs[idx]));
+      finish(A, rhs * A.nf + it.ooff + j, outs[idx]);
     }
   }
   __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
     for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
       const int rhs = idx / A.q2, j = idx % A.q2;
-      finish(A, rhs * A.nf + it.ooff + j, make_double2(0.0, 0.0));
+      finish(A, rhs * A.nf + it.ooff + j, czero<Acc>());
     }
   }
 };
@@ -137,6 +182,7 @@ struct RhsP {
     it.mat = A.H + (long long)it.leaf * A.nb * A.ldH + (long long)it.face * A.q2 * A.ldH;
     it.ld = A.ldH;
     it.ncols = A.ni;
+    it.nrows = A.q2;
     it.xoff = (long long)it.leaf * A.ni;
     return true;
   }
@@ -164,6 +210,7 @@ struct PrecBP {
   using Acc = typename MT<TM>::Acc;
   struct Args {
     const TM* B;
+    const float* bscale;  // FP16 blocks: row scales, index (leaf*6 + face)*q2 + j
     const long long* b_off;
     const uint8_t* int_mask;
     const int* lf_slot;
@@ -176,48 +223,55 @@ struct PrecBP {
     int nrhs;
     long long nitems;
   };
+  // One item per leaf: the rows of all its internal faces (B^leaf) against the
+  // values on its external faces, plus the copy of the external faces.
   __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
-    it.leaf = (int)(item / 6);
-    it.face = (int)(item % 6);
+    it.leaf = (int)item;
     const int mask = A.int_mask[it.leaf];
     it.mask = mask;
     it.xoff = (long long)it.leaf * A.nb;
-    if (!(mask & (1 << it.face))) {
-      it.ooff = it.xoff + (long long)it.face * A.q2;
-      return false;
-    }
-    const int rb = __popc(mask & ((1 << it.face) - 1));
-    const int next = 6 - __popc(mask);
-    it.ncols = next * A.q2;
+    const int nint = __popc(mask);
+    if (nint == 0) return false;
+    it.nrows = nint * A.q2;
+    it.ncols = (6 - nint) * A.q2;
     it.ld = (int)rup4(it.ncols);
-    it.mat = A.B + A.b_off[it.leaf] + (long long)rb * A.q2 * it.ld;
-    it.nbr = A.g.neighbor(it.leaf, it.face);
-    it.aoff = (long long)it.nbr * A.nb + (long long)(it.face ^ 1) * A.q2;
-    it.ooff = (long long)A.lf_slot[it.nbr * 6 + (it.face ^ 1)] * A.q2;
+    it.mat = A.B + A.b_off[it.leaf];
     return true;
   }
-  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
-    int e = c / A.q2;
-    int f = 0;
-    for (; f < 6; ++f)
-      if (!(it.mask & (1 << f))) {
-        if (e == 0) break;
-        --e;
+  // k-th set (internal) or clear (external) face bit of the mask
+  __device__ static int nth_face(int mask, int k, bool internal) {
+    for (int f = 0; f < 6; ++f)
+      if (((mask >> f) & 1) == (internal ? 1 : 0)) {
+        if (k == 0) return f;
+        --k;
       }
+    return 5;
+  }
+  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
+    const int f = nth_face(it.mask, c / A.q2, false);
     return cvt<Acc>(A.r[rhs * A.nf + it.xoff + (long long)f * A.q2 + c % A.q2]);
   }
   __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
-    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
-      const int rhs = idx / A.q2, j = idx % A.q2;
-      const double2 v = csub(cvt<double2>(A.r[rhs * A.nf + it.aoff + j]), cvt<double2>(outs[idx]));
-      A.t[rhs * A.tstride + it.ooff + j] = cvt<TOUT>(v);
+    for (int idx = tid; idx < nr * it.nrows; idx += kThreads) {
+      const int rhs = idx / it.nrows, row = idx % it.nrows;
+      const int face = nth_face(it.mask, row / A.q2, true), j = row % A.q2;
+      const int nbr = A.g.neighbor(it.leaf, face);
+      const long long aoff = (long long)nbr * A.nb + (long long)(face ^ 1) * A.q2;
+      const long long ooff = (long long)A.lf_slot[nbr * 6 + (face ^ 1)] * A.q2;
+      const Acc g = rscale(outs[idx], A.bscale, ((long long)it.leaf * 6 + face) * A.q2 + j);
+      const Acc v = csub(cvt<Acc>(A.r[rhs * A.nf + aoff + j]), g);
+      A.t[rhs * A.tstride + ooff + j] = cvt<TOUT>(v);
     }
+    copy(A, it, nr, tid);
   }
+  // z = r on the faces leaving the leaf's cluster
   __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
-    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
-      const int rhs = idx / A.q2, j = idx % A.q2;
-      const long long o = rhs * A.nf + it.ooff + j;
-      A.z[o] = cvt<TOUT>(cvt<double2>(A.r[o]));
+    const int next = 6 - __popc(it.mask);
+    for (int idx = tid; idx < nr * next * A.q2; idx += kThreads) {
+      const int rhs = idx / (next * A.q2), e = idx % (next * A.q2);
+      const int face = nth_face(it.mask, e / A.q2, false);
+      const long long o = rhs * A.nf + it.xoff + (long long)face * A.q2 + e % A.q2;
+      A.z[o] = cvt<TOUT>(cvt<Acc>(A.r[o]));
     }
   }
 };
@@ -228,6 +282,7 @@ struct PrecKP {
   using Acc = typename MT<TM>::Acc;
   struct Args {
     const TM* K;
+    const float* kscale;  // FP16 blocks: row scales, index slot*q2 + j
     const long long* kc_off;
     const int* cl_slot_begin;
     const int* slot_cluster;
@@ -246,9 +301,11 @@ struct PrecKP {
     it.ncols = ns * A.q2;
     it.ld = (int)rup4(it.ncols);
     it.mat = A.K + A.kc_off[c] + (long long)(gs - s0) * A.q2 * it.ld;
+    it.nrows = A.q2;
     it.xoff = (long long)s0 * A.q2;
     const int lf = A.slot_lf[gs];
     it.ooff = (long long)(lf / 6) * A.nb + (long long)(lf % 6) * A.q2;
+    it.aoff = (long long)gs * A.q2;
     return true;
   }
   __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
@@ -257,7 +314,7 @@ struct PrecKP {
   __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
     for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
       const int rhs = idx / A.q2, j = idx % A.q2;
-      A.z[rhs * A.nf + it.ooff + j] = cvt<TOUT>(cvt<double2>(outs[idx]));
+      A.z[rhs * A.nf + it.ooff + j] = cvt<TOUT>(rscale(outs[idx], A.kscale, it.aoff + j));
     }
   }
   __device__ static void copy(const Args&, const ItemInfo&, int, int) {}
@@ -267,16 +324,15 @@ struct PrecKP {
 // The kernel.
 // ---------------------------------------------------------------------------
 template <class P, int NR, int RPW>
-__global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Args A, int xcap) {
+__global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Args A, int xcap, int rowcap) {
   using TM = typename P::TM;
   using Acc = typename P::Acc;
   constexpr int VPL = MT<TM>::VPL;
   extern __shared__ __align__(16) unsigned char smraw[];
   Acc* xs = reinterpret_cast<Acc*>(smraw);
-  Acc* outs = xs + NR * xcap;
+  Acc* outs = xs + NR * xcap;  // NR x rowcap
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nr = A.nrhs < NR ? A.nrhs : NR;
-  const int q2 = A.q2;
   for (long long item = blockIdx.x; item < A.nitems; item += gridDim.x) {
     ItemInfo it;
     if (!P::decode(A, item, it)) {
@@ -290,7 +346,8 @@ __global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Ar
     }
     __syncthreads();
     const TM* mat = reinterpret_cast<const TM*>(it.mat);
-    for (int r0 = warp * RPW; r0 < q2; r0 += kWarps * RPW) {
+    const int nrows = it.nrows;
+    for (int r0 = warp * RPW; r0 < nrows; r0 += kWarps * RPW) {
       Acc acc[RPW][NR];
 #pragma unroll
       for (int i = 0; i < RPW; ++i)
@@ -298,14 +355,14 @@ __global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Ar
         for (int rr = 0; rr < NR; ++rr) acc[i][rr] = czero<Acc>();
 #pragma unroll 2
       for (int c = lane * VPL; c < ncp; c += 32 * VPL) {
-        TM mv[RPW][VPL];
+        Acc mv[RPW][VPL];
 #pragma unroll
         for (int i = 0; i < RPW; ++i) {
-          if (r0 + i < q2) {
+          if (r0 + i < nrows) {
             MT<TM>::load(mat + (long long)(r0 + i) * it.ld + c, mv[i]);
           } else {
 #pragma unroll
-            for (int v = 0; v < VPL; ++v) mv[i][v] = czero<TM>();
+            for (int v = 0; v < VPL; ++v) mv[i][v] = czero<Acc>();
           }
         }
 #pragma unroll
@@ -328,9 +385,9 @@ __global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Ar
       if (lane == 0) {
 #pragma unroll
         for (int i = 0; i < RPW; ++i)
-          if (r0 + i < q2)
+          if (r0 + i < nrows)
 #pragma unroll
-            for (int rr = 0; rr < NR; ++rr) outs[rr * q2 + r0 + i] = acc[i][rr];
+            for (int rr = 0; rr < NR; ++rr) outs[rr * nrows + r0 + i] = acc[i][rr];
       }
     }
     __syncthreads();
@@ -340,9 +397,9 @@ __global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Ar
 }
 
 template <class P, int NR, int RPW>
-cudaError_t launch_one(const typename P::Args& A, int xcap, int q2, int nsm, cudaStream_t st, long long* counter) {
+cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm, cudaStream_t st, long long* counter) {
   using Acc = typename P::Acc;
-  const size_t smem = ((size_t)NR * xcap + (size_t)NR * q2) * sizeof(Acc);
+  const size_t smem = ((size_t)NR * xcap + (size_t)NR * rowcap) * sizeof(Acc);
   auto kern = seg_gemv_kernel<P, NR, RPW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -352,14 +409,14 @@ cudaError_t launch_one(const typename P::Args& A, int xcap, int q2, int nsm, cud
   occ = std::max(occ, 1);
   long long grid = std::min<long long>(A.nitems, (long long)nsm * occ);
   if (grid <= 0) return cudaSuccess;
-  kern<<<(unsigned)grid, kThreads, smem, st>>>(A, xcap);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(A, xcap, rowcap);
   ++*counter;
   return cudaGetLastError();
 }
 
 // Launch over right-hand-side groups of at most 8 (each group re-reads the matrix).
 template <class P, class Shift>
-cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int xcap, int q2, cudaStream_t st,
+cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int xcap, int rowcap, cudaStream_t st,
                           Shift shift) {
   const int nsm = h->nsm;
   long long* counter = &h->prof.launches;
@@ -369,10 +426,10 @@ cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int
     shift(B, r0);
     B.nrhs = nr;
     cudaError_t e;
-    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, q2, nsm, st, counter);
-    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, q2, nsm, st, counter);
-    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, q2, nsm, st, counter);
-    else e = launch_one<P, 8, 1>(B, xcap, q2, nsm, st, counter);
+    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, rowcap, nsm, st, counter);
+    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, rowcap, nsm, st, counter);
+    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, rowcap, nsm, st, counter);
+    else e = launch_one<P, 8, 1>(B, xcap, rowcap, nsm, st, counter);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -411,13 +468,14 @@ cudaError_t apply_t(const hps_handle* h, const TM* R, const TIN* f, TOUT* y, con
 
 template <class TM, class TIN, class TOUT>
 cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* r, TOUT* z, TOUT* t, int nrhs,
-                      cudaStream_t st) {
+                      cudaStream_t st, const float* bscale = nullptr, const float* kscale = nullptr) {
   const int q2 = h->q * h->q;
   const long long tstride = (long long)h->ct.nslots * q2;
   {
     using P = PrecBP<TM, TIN, TOUT>;
     typename P::Args A;
     A.B = B;
+    A.bscale = bscale;
     A.b_off = h->dct.b_off;
     A.int_mask = h->dct.int_mask;
     A.lf_slot = h->dct.lf_slot;
@@ -430,9 +488,9 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.nf = h->nf;
     A.tstride = tstride;
     A.nrhs = nrhs;
-    A.nitems = (long long)h->nl * 6;
+    A.nitems = (long long)h->nl;
     cudaEvent_t ev = h->prof.begin(st);
-    cudaError_t e = launch_groups<P>(h, A, nrhs, xcap_of(h), q2, st, [&](typename P::Args& X, int r0) {
+    cudaError_t e = launch_groups<P>(h, A, nrhs, xcap_of(h), h->nb, st, [&](typename P::Args& X, int r0) {
       X.r += (long long)r0 * h->nf;
       X.z += (long long)r0 * h->nf;
       X.t += (long long)r0 * tstride;
@@ -445,6 +503,7 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     using P = PrecKP<TM, TOUT, TOUT>;
     typename P::Args A;
     A.K = K;
+    A.kscale = kscale;
     A.kc_off = h->dct.cl_kc_off;
     A.cl_slot_begin = h->dct.cl_slot_begin;
     A.slot_cluster = h->dct.slot_cluster;
@@ -477,12 +536,22 @@ cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const
       return apply_t(h, h->R64, (const double2*)f, (double2*)y, bvec, nrhs, st);
     return cudaErrorInvalidValue;
   }
+  const bool tc = h->opt.tc_apply && h->tc_error && nrhs >= 64 && nrhs % 64 == 0 && !bvec;
+  if (tc && tin == VType::C64 && tout == VType::C64)
+    return launch_apply_tc(h, (const float2*)f, y, false, nrhs, h->tc_error, st);
+  if (tc && tin == VType::C64 && tout == VType::DF)
+    return launch_apply_tc(h, (const float2*)f, y, true, nrhs, h->tc_error, st);
   if (tin == VType::C64 && tout == VType::C64)
     return apply_t(h, h->R32, (const float2*)f, (float2*)y, bvec, nrhs, st);
+  if (bvec) return cudaErrorInvalidValue;
   if (tin == VType::C64 && tout == VType::C128)
-    return apply_t(h, h->R32, (const float2*)f, (double2*)y, bvec, nrhs, st);
+    return apply_t(h, h->R32, (const float2*)f, (double2*)y, nullptr, nrhs, st);
   if (tin == VType::C128 && tout == VType::C128)
-    return apply_t(h, h->R32, (const double2*)f, (double2*)y, bvec, nrhs, st);
+    return apply_t(h, h->R32, (const double2*)f, (double2*)y, nullptr, nrhs, st);
+  if (tin == VType::C64 && tout == VType::DF)
+    return apply_t(h, h->R32, (const float2*)f, (float4*)y, nullptr, nrhs, st);
+  if (tin == VType::DF && tout == VType::DF)
+    return apply_t(h, h->R32, (const float4*)f, (float4*)y, nullptr, nrhs, st);
   return cudaErrorInvalidValue;
 }
 
@@ -518,15 +587,25 @@ cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, 
 }
 
 cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, const void* r, VType tout, void* z,
-                           void* scratch, int nrhs, cudaStream_t st) {
+                           void* scratch, int nrhs, cudaStream_t st, bool fp16_blocks) {
   if (!fp32_matrix) {
     if (tin == VType::C128 && tout == VType::C128)
       return precond_t(h, h->B64, h->Kc64, (const double2*)r, (double2*)z, (double2*)scratch, nrhs, st);
     return cudaErrorInvalidValue;
   }
   if (tout != VType::C64) return cudaErrorInvalidValue;
+  if (fp16_blocks) {
+    if (!h->Kc16 || !h->B16) return cudaErrorInvalidValue;
+    if (tin == VType::C64)
+      return precond_t(h, h->B16, h->Kc16, (const float2*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s);
+    if (tin == VType::DF)
+      return precond_t(h, h->B16, h->Kc16, (const float4*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s);
+    return precond_t(h, h->B16, h->Kc16, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s);
+  }
   if (tin == VType::C64)
     return precond_t(h, h->B32, h->Kc32, (const float2*)r, (float2*)z, (float2*)scratch, nrhs, st);
+  if (tin == VType::DF)
+    return precond_t(h, h->B32, h->Kc32, (const float4*)r, (float2*)z, (float2*)scratch, nrhs, st);
   return precond_t(h, h->B32, h->Kc32, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st);
 }
 

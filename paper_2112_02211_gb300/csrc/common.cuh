@@ -29,6 +29,18 @@ __host__ __device__ __forceinline__ double2 cinv(double2 a) {
 }
 
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cinv(float2 a) {
+  if (fabsf(a.x) >= fabsf(a.y)) {
+    float r = a.y / a.x, d = a.x + a.y * r;
+    return make_float2(1.0f / d, -r / d);
+  } else {
+    float r = a.x / a.y, d = a.y + a.x * r;
+    return make_float2(r / d, -1.0f / d);
+  }
+}
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 // Accumulate acc += a * b (complex), in the accumulator's precision.
@@ -45,6 +57,60 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
+// ---- double-float arithmetic ---------------------------------------------------
+// A value a = h + l held as two FP32 numbers with |l| <= ulp(h)/2 (about 48
+// significant bits).  Error-free transformations: Knuth's TwoSum, Dekker's
+// Fast2Sum (|a| >= |b|) and the FMA-based TwoProduct.  The _rn intrinsics keep
+// the compiler from contracting or reassociating these sequences.
+struct dfr {
+  float h, l;
+};
+__device__ __forceinline__ dfr df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfr df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfr df_add(dfr a, dfr b) {
+  dfr s = df_two_sum(a.h, b.h);
+  return df_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfr df_neg(dfr a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dfr df_mul(dfr a, dfr b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfr df_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(dfr a) { return (double)a.h + (double)a.l; }
+
+// Complex double-float, stored as float4 (re.h, im.h, re.l, im.l): 16 bytes.
+struct dfc {
+  dfr re, im;
+};
+__device__ __forceinline__ dfc dfc_load(float4 v) { return {{v.x, v.z}, {v.y, v.w}}; }
+__device__ __forceinline__ float4 dfc_store(dfc a) { return make_float4(a.re.h, a.im.h, a.re.l, a.im.l); }
+__device__ __forceinline__ dfc dfc_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))}; }
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
+  return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+// conj(a) * b
+__device__ __forceinline__ dfc dfc_conjmul(dfc a, dfc b) {
+  return {df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_neg(df_mul(a.im, b.re)))};
+}
+__device__ __forceinline__ dfc dfc_from(double2 v) { return {df_from_double(v.x), df_from_double(v.y)}; }
+__device__ __forceinline__ double2 dfc_to_double2(dfc a) { return make_double2(df_to_double(a.re), df_to_double(a.im)); }
+
 // ---- conversions ------------------------------------------------------------
 template <class T> struct Real;
 template <> struct Real<double2> { using type = double; };
@@ -59,6 +125,13 @@ template <> __device__ __forceinline__ double2 cvt<double2, float2>(float2 v) {
 template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 v) {
   return make_float2((float)v.x, (float)v.y);
 }
+
+template <> __device__ __forceinline__ float2 cvt<float2, float4>(float4 v) { return make_float2(v.x, v.y); }
+template <> __device__ __forceinline__ double2 cvt<double2, float4>(float4 v) {
+  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+template <> __device__ __forceinline__ float4 cvt<float4, float2>(float2 v) { return make_float4(v.x, v.y, 0.f, 0.f); }
+template <> __device__ __forceinline__ float4 cvt<float4, double2>(double2 v) { return dfc_store(dfc_from(v)); }
 
 template <class T> __device__ __forceinline__ T czero();
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }

@@ -2,6 +2,7 @@
 // launchers implemented in setup.cu, apply.cu and krylov.cu.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -180,6 +181,7 @@ struct hps_handle {
   float2* R32 = nullptr;   // nl x nb x ldR
   double2* H64 = nullptr;  // nl x nb x ldH
   double2* lambda = nullptr;  // nl
+  double2* cdiag = nullptr;   // nl x ni: C = kappa^2 (1 - b) at interior nodes (kept for recovery)
 
   // preconditioner
   bool has_precond = false;
@@ -189,8 +191,13 @@ struct hps_handle {
   float2* Kc32 = nullptr;
   double2* B64 = nullptr;
   float2* B32 = nullptr;
+  __half2* Kc16 = nullptr;  // FP16 copies, row r scaled by 1/Kc16s[r] (global row = slot*q^2 + j)
+  float* Kc16s = nullptr;
+  __half2* B16 = nullptr;   // FP16 copies of B, rows scaled by 1/B16s[(leaf*6+face)*q^2 + j]
+  float* B16s = nullptr;
   void* pc_scratch = nullptr;  // nslots*q^2*max_rhs complex double (precond t buffer)
 
+  int* tc_error = nullptr;  // device error word of the tensor-core kernels
   hps::KrylovSpace ks;
   mutable hps::Profiler prof;
   size_t bytes = 0;
@@ -206,10 +213,16 @@ cudaError_t launch_nodes(const double* tables, const TableLayout& tl, int nx, in
 // Builds R (and H) for all leaves; see setup.cu.
 int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st);
 int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st);
+int build_precond_fp16(hps_handle* h, cudaStream_t st);
+int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, cudaStream_t st);
+size_t workspace_cap(const hps_handle* h);
+size_t exact_maps_workspace(const hps_handle* h, size_t budget, int* nbatch_out);
+size_t precond_workspace(const hps_handle* h, size_t budget, int* cb_out);
 void build_cluster_tables(hps_handle* h, int width);
 
 // ---- apply.cu ----
-enum class VType { C128, C64 };
+// C128 complex double, C64 complex float, DF complex double-float (float4: re.h, im.h, re.l, im.l)
+enum class VType { C128, C64, DF };
 // y = (I + Pi R) f  (mode 0) or y = b - (I + Pi R) f (mode 1), R in FP64 or FP32.
 cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const void* f,
                          VType tout, void* y, const double2* bvec, int nrhs, bool residual,
@@ -217,7 +230,11 @@ cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const
 cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
                        cudaStream_t st);
 cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, const void* r,
-                           VType tout, void* z, void* scratch, int nrhs, cudaStream_t st);
+                           VType tout, void* z, void* scratch, int nrhs, cudaStream_t st, bool fp16_blocks = false);
+// Tensor-core apply for 64-RHS groups (tc_apply.cu); f complex float, y complex
+// float or double-float; nrhs a multiple of 64.
+cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool out_df, int nrhs, int* d_error,
+                            cudaStream_t st);
 // Timed wrappers (phase intervals recorded when profiling is on).
 cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType tin, const void* f, VType tout,
                         void* y, const double2* bvec, int nrhs, bool residual, cudaStream_t st);

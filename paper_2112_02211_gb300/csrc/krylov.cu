@@ -14,7 +14,7 @@
 // correction equation with the FP32 operator and the FP64 residual drives the
 // next cycle (iterative refinement with a GMRES inner solver).
 //
-// Dot products are formed as fixed-order block partials (2048 entries per
+// Dot products are formed as fixed-order block partials (512 entries per
 // block, warp shuffles, then a sequential sum over blocks), so results are
 // bitwise reproducible run to run.
 #include <algorithm>
@@ -30,7 +30,7 @@ namespace hps {
 namespace {
 
 constexpr int kT = 256;      // threads per block
-constexpr int kE = 8;        // elements per thread
+constexpr int kE = 2;        // vector entries per thread (512 per block: enough blocks to fill the GPU)
 constexpr int kChunk = kT * kE;
 constexpr int kG = 8;        // vectors per register group
 
@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kT) axpy_kernel(VecArgs a, int mode) {
     const long long i = base + (long long)e * kT;
     wv[e] = (i < a.nf) ? w[i] : make_double2(0.0, 0.0);
   }
+#pragma unroll 4
   for (int j = 0; j < a.nvec; ++j) {
     const double2* v = a.V + ((long long)j * a.nrhs + rhs) * a.nf;
     const double2 c = cf[j];
@@ -166,6 +167,162 @@ __global__ void __launch_bounds__(kT) axpy_kernel(VecArgs a, int mode) {
 #pragma unroll
     for (int e = 0; e < kE; ++e) acc[0].x += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
     block_reduce_store(acc, 1, out);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float variants (mixed form).  The basis is stored as complex
+// double-float (float4 per entry, 16 bytes like complex double) and every
+// per-entry operation runs on the FP32 pipe; block partials leave as FP64.
+// ---------------------------------------------------------------------------
+struct DfArgs {
+  const float4* V;  // vector j of rhs r at V + (j*nrhs + r)*nf
+  float4* w;
+  long long nf;
+  int nrhs, nvec, M1, nblk;
+  double2* part;
+  const double2* coef;
+  int cstride;
+  const int* active;
+};
+
+// Warp-level double-float sums, then one FP64 value per warp, summed over the
+// warps in a fixed order.
+__device__ __forceinline__ void block_reduce_store_df(dfc (&acc)[kG], int ng, double2* out) {
+  __shared__ double2 red[kT / 32][kG];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < kG; ++g) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dfc other;
+      other.re.h = __shfl_xor_sync(0xffffffffu, acc[g].re.h, o);
+      other.re.l = __shfl_xor_sync(0xffffffffu, acc[g].re.l, o);
+      other.im.h = __shfl_xor_sync(0xffffffffu, acc[g].im.h, o);
+      other.im.l = __shfl_xor_sync(0xffffffffu, acc[g].im.l, o);
+      acc[g] = dfc_add(acc[g], other);
+    }
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int g = 0; g < kG; ++g) red[warp][g] = dfc_to_double2(acc[g]);
+  __syncthreads();
+  if (threadIdx.x < ng) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int w = 0; w < kT / 32; ++w) s = cadd(s, red[w][threadIdx.x]);
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void df_dots(const DfArgs& a, int rhs, long long base, const dfc (&wv)[kE], double2* out) {
+  for (int g0 = 0; g0 < a.nvec; g0 += kG) {
+    const int ng = min(kG, a.nvec - g0);
+    dfc acc[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) acc[g] = dfc_zero();
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      if (g < ng) {
+        const float4* v = a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf;
+#pragma unroll
+        for (int e = 0; e < kE; ++e) {
+          const long long i = base + (long long)e * kT;
+          if (i < a.nf) acc[g] = dfc_add(acc[g], dfc_conjmul(dfc_load(v[i]), wv[e]));
+        }
+      }
+    }
+    block_reduce_store_df(acc, ng, out + g0);
+  }
+}
+
+__global__ void __launch_bounds__(kT) mdot_df_kernel(DfArgs a) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (a.active && !a.active[rhs]) return;
+  const long long base = (long long)blk * kChunk + threadIdx.x;
+  const float4* w = a.w + rhs * a.nf;
+  dfc wv[kE];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const long long i = base + (long long)e * kT;
+    wv[e] = (i < a.nf) ? dfc_load(w[i]) : dfc_zero();
+  }
+  df_dots(a, rhs, base, wv, a.part + ((long long)rhs * a.nblk + blk) * a.M1);
+}
+
+// w -= V coef; then (mode 1) partial dots V^H w, or (mode 2) partial ||w||^2.
+__global__ void __launch_bounds__(kT) axpy_df_kernel(DfArgs a, int mode) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (a.active && !a.active[rhs]) return;
+  __shared__ dfc cf[64];
+  for (int j = threadIdx.x; j < a.nvec; j += kT) cf[j] = dfc_from(a.coef[(long long)rhs * a.cstride + j]);
+  __syncthreads();
+  const long long base = (long long)blk * kChunk + threadIdx.x;
+  float4* w = a.w + rhs * a.nf;
+  dfc wv[kE];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const long long i = base + (long long)e * kT;
+    wv[e] = (i < a.nf) ? dfc_load(w[i]) : dfc_zero();
+  }
+#pragma unroll 4
+  for (int j = 0; j < a.nvec; ++j) {
+    const float4* v = a.V + ((long long)j * a.nrhs + rhs) * a.nf;
+    const dfc c = cf[j];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      const long long i = base + (long long)e * kT;
+      if (i < a.nf) wv[e] = dfc_sub(wv[e], dfc_mul(c, dfc_load(v[i])));
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const long long i = base + (long long)e * kT;
+    if (i < a.nf) w[i] = dfc_store(wv[e]);
+  }
+  double2* out = a.part + ((long long)rhs * a.nblk + blk) * a.M1;
+  if (mode == 1) {
+    df_dots(a, rhs, base, wv, out);
+  } else if (mode == 2) {
+    dfc acc[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) acc[g] = dfc_zero();
+#pragma unroll
+    for (int e = 0; e < kE; ++e)
+      acc[0].re = df_add(acc[0].re, df_add(df_mul(wv[e].re, wv[e].re), df_mul(wv[e].im, wv[e].im)));
+    block_reduce_store_df(acc, 1, out);
+  }
+}
+
+// w <- w * invn[rhs] in double-float
+__global__ void scale_df_kernel(float4* w, long long nf, const double* invn) {
+  const int rhs = blockIdx.y;
+  const dfr s = df_from_double(invn[rhs]);
+  float4* p = w + rhs * nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
+    const dfc v = dfc_load(p[i]);
+    p[i] = dfc_store(dfc{df_mul(v.re, s), df_mul(v.im, s)});
+  }
+}
+
+// dst (double-float) = src (complex double) * invn[rhs]
+__global__ void scale_copy_df_kernel(const double2* src, float4* dst, long long nf, const double* invn) {
+  const int rhs = blockIdx.y;
+  const double s = invn[rhs];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x)
+    dst[rhs * nf + i] = dfc_store(dfc_from(cscale(src[rhs * nf + i], s)));
+}
+
+// u (complex double) = sum_{j<kmax} y_j v_j, accumulated in double-float
+__global__ void combine_df_kernel(const float4* V, int nrhs, long long nf, int kmax, int m, const double2* y, double2* u) {
+  const int rhs = blockIdx.y;
+  __shared__ dfc ys[64];
+  for (int j = threadIdx.x; j < kmax; j += blockDim.x) ys[j] = dfc_from(y[(long long)rhs * m + j]);
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
+    dfc s = dfc_zero();
+    for (int j = 0; j < kmax; ++j) s = dfc_add(s, dfc_mul(ys[j], dfc_load(V[((long long)j * nrhs + rhs) * nf + i])));
+    u[rhs * nf + i] = dfc_to_double2(s);
   }
 }
 
@@ -494,7 +651,10 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
         HPS_CUDA_TRY(cudaMemcpyAsync(k.g + (long long)r * M1, &g0[r], sizeof(double2), cudaMemcpyHostToDevice, st));
       HPS_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    scale_copy_kernel<<<vgrid, 256, 0, st>>>(k.r, k.V, nf, invn);
+    if (mixed)
+      scale_copy_df_kernel<<<vgrid, 256, 0, st>>>(k.r, (float4*)k.V, nf, invn);
+    else
+      scale_copy_kernel<<<vgrid, 256, 0, st>>>(k.r, k.V, nf, invn);
     HPS_CUDA_TRY(cudaGetLastError());
     h->prof.launches += 1;
     int jdone = 0;
@@ -504,10 +664,10 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       // z = M^{-1} v_j ; w = A z
       if (mixed) {
         if (pc) {
-          HPS_CUDA_TRY(launch_precond(h, true, VType::C128, vj, VType::C64, k.z, k.zt, nrhs, st));
-          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::C64, k.z, VType::C128, w, nullptr, nrhs, false, st));
+          HPS_CUDA_TRY(launch_precond(h, true, VType::DF, vj, VType::C64, k.z, k.zt, nrhs, st, h->Kc16 != nullptr));
+          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::C64, k.z, VType::DF, w, nullptr, nrhs, false, st));
         } else {
-          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
+          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::DF, vj, VType::DF, w, nullptr, nrhs, false, st));
         }
       } else {
         if (pc) {
@@ -528,20 +688,33 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       va.part = k.part;
       va.active = active;
       const dim3 bgrid(k.nblk, nrhs);
+      DfArgs da;
+      da.V = (const float4*)k.V;
+      da.w = (float4*)w;
+      da.nf = nf;
+      da.nrhs = nrhs;
+      da.nvec = j + 1;
+      da.M1 = M1;
+      da.nblk = k.nblk;
+      da.part = k.part;
+      da.active = active;
       cudaEvent_t ev_arn = h->prof.begin(st);
-      mdot_kernel<<<bgrid, kT, 0, st>>>(va);
+      if (mixed) mdot_df_kernel<<<bgrid, kT, 0, st>>>(da);
+      else mdot_kernel<<<bgrid, kT, 0, st>>>(va);
       HPS_CUDA_TRY(cudaGetLastError());
       reduce_kernel<<<dim3(j + 1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, k.hcol, M1 + 1, 0, active);
       HPS_CUDA_TRY(cudaGetLastError());
-      va.coef = k.hcol;
-      va.cstride = M1 + 1;
-      axpy_kernel<<<bgrid, kT, 0, st>>>(va, 1);
+      va.coef = da.coef = k.hcol;
+      va.cstride = da.cstride = M1 + 1;
+      if (mixed) axpy_df_kernel<<<bgrid, kT, 0, st>>>(da, 1);
+      else axpy_kernel<<<bgrid, kT, 0, st>>>(va, 1);
       HPS_CUDA_TRY(cudaGetLastError());
       reduce_kernel<<<dim3(j + 1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, h2, M1, 0, active);
       HPS_CUDA_TRY(cudaGetLastError());
-      va.coef = h2;
-      va.cstride = M1;
-      axpy_kernel<<<bgrid, kT, 0, st>>>(va, 2);
+      va.coef = da.coef = h2;
+      va.cstride = da.cstride = M1;
+      if (mixed) axpy_df_kernel<<<bgrid, kT, 0, st>>>(da, 2);
+      else axpy_kernel<<<bgrid, kT, 0, st>>>(va, 2);
       HPS_CUDA_TRY(cudaGetLastError());
       reduce_kernel<<<dim3(1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, k.hcol + M1, M1 + 1, 0, active);
       HPS_CUDA_TRY(cudaGetLastError());
@@ -567,7 +740,8 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       ga.any_active = any_active;
       givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(ga);
       HPS_CUDA_TRY(cudaGetLastError());
-      scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);
+      if (mixed) scale_df_kernel<<<vgrid, 256, 0, st>>>((float4*)w, nf, invn);
+      else scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);
       HPS_CUDA_TRY(cudaGetLastError());
       h->prof.end(HPS_PHASE_ARNOLDI, ev_arn, st);
       h->prof.launches += 8;
@@ -582,12 +756,13 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     cudaEvent_t ev_up = h->prof.begin(st);
     lsq_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, m, M1, k.H, k.g, kcount, k.y);
     HPS_CUDA_TRY(cudaGetLastError());
-    combine_kernel<<<vgrid, 256, 0, st>>>(k.V, nrhs, nf, jdone, m, k.y, k.u);
+    if (mixed) combine_df_kernel<<<vgrid, 256, 0, st>>>((const float4*)k.V, nrhs, nf, jdone, m, k.y, k.u);
+    else combine_kernel<<<vgrid, 256, 0, st>>>(k.V, nrhs, nf, jdone, m, k.y, k.u);
     HPS_CUDA_TRY(cudaGetLastError());
     const long long nall = (long long)nrhs * nf;
     if (pc) {
       if (mixed) {
-        HPS_CUDA_TRY(launch_precond(h, true, VType::C128, k.u, VType::C64, k.z, k.zt, nrhs, st));
+        HPS_CUDA_TRY(launch_precond(h, true, VType::C128, k.u, VType::C64, k.z, k.zt, nrhs, st, h->Kc16 != nullptr));
         xpy_kernel<float2><<<4 * h->nsm, 256, 0, st>>>(x, (const float2*)k.z, nall);
       } else {
         HPS_CUDA_TRY(launch_precond(h, false, VType::C128, k.u, VType::C128, k.z, k.zt, nrhs, st));
@@ -602,6 +777,14 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     // true residual with the FP64 maps
     HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_RESIDUAL, false, VType::C128, x, VType::C128, k.r, b, nrhs, true, st));
     if ((rc = vec_norms(h, k.r, nrhs, rnorm, st))) return rc;
+    if (h->tc_error) {
+      int terr = 0;
+      HPS_CUDA_TRY(cudaMemcpy(&terr, h->tc_error, sizeof(int), cudaMemcpyDeviceToHost));
+      if (terr) {
+        set_error("tensor-core apply: a bounded wait gave up");
+        return HPS_ETIMEOUT;
+      }
+    }
     ++cycles;
   }
   double rel = 0.0;

@@ -191,21 +191,22 @@ __device__ __forceinline__ int gidx(int i, int j, int k, int p, int n1, int ni) 
 
 // ---------------------------------------------------------------------------
 // Leaf matrix assembly into a zeroed row-major workspace (one thread per row).
-// Columns [0, n): A; [n, n+nb): e_{boundary}; [n+nb, n+nb+ni): e_{interior}
-// (only when with_h).  Interior rows take C from cdiag, or the leaf constant
+// Columns [0, n): A; with ecols >= 1 also [n, n+nb): e_{boundary}; with
+// ecols == 2 also [n+nb, n+nb+ni): e_{interior}.  Interior rows take C from cdiag, or the leaf constant
 // lam[leaf] for the homogenized operator.
 // ---------------------------------------------------------------------------
-__global__ void assemble_kernel(double2* W, long long wstride, int ld, const int* leaf_ids, int leaf0,
-                                int nbatch, const double* T, TableLayout tl, double eta,
-                                const double2* cdiag, const double2* lam, int with_h) {
+template <class T>
+__global__ void assemble_kernel(T* W, long long wstride, int ld, const int* leaf_ids, int leaf0,
+                                int nbatch, const double* tab, TableLayout tl, double eta,
+                                const double2* cdiag, const double2* lam, int ecols) {
   const int p = tl.p, n1 = p - 2, ni = n1 * n1 * n1, nb = 6 * n1 * n1, n = ni + nb;
   const int b = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbatch || r >= n) return;
   const int leaf = leaf_ids ? leaf_ids[b] : leaf0 + b;
-  double2* row = W + (long long)b * wstride + (long long)r * ld;
-  const double* D = T + tl.D;
-  const double* D2 = T + tl.D2;
+  T* row = W + (long long)b * wstride + (long long)r * ld;
+  const double* D = tab + tl.D;
+  const double* D2 = tab + tl.D2;
   if (r < ni) {
     const int i = r % n1 + 1, j = (r / n1) % n1 + 1, k = r / (n1 * n1) + 1;
     for (int m = 0; m < p; ++m) {
@@ -216,7 +217,7 @@ __global__ void assemble_kernel(double2* W, long long wstride, int ld, const int
     const double2 c = lam ? lam[leaf] : cdiag[(long long)leaf * ni + r];
     row[r].x -= c.x;
     row[r].y -= c.y;
-    if (with_h) row[n + nb + r].x = 1.0;
+    if (ecols == 2) row[n + nb + r].x = 1.0;
   } else {
     const int jb = r - ni;
     const int face = jb / (n1 * n1), rem = jb % (n1 * n1);
@@ -234,7 +235,7 @@ __global__ void assemble_kernel(double2* W, long long wstride, int ld, const int
       row[gidx(q3[0], q3[1], q3[2], p, n1, ni)].x += sg * D[axis * p * p + e * p + m];
     }
     row[r].y += eta;
-    row[n + jb].x = 1.0;
+    if (ecols >= 1) row[n + jb].x = 1.0;
   }
 }
 
@@ -244,21 +245,22 @@ __global__ void assemble_kernel(double2* W, long long wstride, int ld, const int
 // [gj0, k) above them, so on exit rows [gj0, n) of columns [n, ncols) hold
 // the corresponding rows of A^{-1} E.  A zero pivot sets *status = 1.
 // ---------------------------------------------------------------------------
-template <int NT>
-__global__ void __launch_bounds__(NT) gj_kernel(double2* W, long long wstride, int ld, int n, int ncols,
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) gj_kernel(T* W, long long wstride, int ld, int n, int ncols,
                                                 int gj0, int nbatch, int* status) {
-  extern __shared__ double2 prow[];
+  extern __shared__ __align__(16) unsigned char gj_smem[];
+  T* prow = reinterpret_cast<T*>(gj_smem);
   __shared__ double sval[NT / 32];
   __shared__ int sidx[NT / 32];
   __shared__ int piv_s;
   if ((int)blockIdx.x >= nbatch) return;
-  double2* M = W + (long long)blockIdx.x * wstride;
+  T* M = W + (long long)blockIdx.x * wstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k < n; ++k) {
     double best = -1.0;
     int bi = n;
     for (int r = k + tid; r < n; r += NT) {
-      double2 v = M[(long long)r * ld + k];
+      const T v = M[(long long)r * ld + k];
       double a = fabs(v.x) + fabs(v.y);
       if (a > best) { best = a; bi = r; }
     }
@@ -289,10 +291,10 @@ __global__ void __launch_bounds__(NT) gj_kernel(double2* W, long long wstride, i
     }
     __syncthreads();
     const int piv = piv_s;
-    double2 pv = M[(long long)piv * ld + k];
-    double2 inv = (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0.0, 0.0) : cinv(pv);
+    const T pv = M[(long long)piv * ld + k];
+    const T inv = (pv.x == 0 && pv.y == 0) ? czero<T>() : cinv(pv);
     for (int c = k + tid; c < ncols; c += NT) {
-      double2 a = M[(long long)piv * ld + c];
+      T a = M[(long long)piv * ld + c];
       if (piv != k) M[(long long)piv * ld + c] = M[(long long)k * ld + c];
       a = cmul(a, inv);
       prow[c] = a;
@@ -302,12 +304,12 @@ __global__ void __launch_bounds__(NT) gj_kernel(double2* W, long long wstride, i
     const int lo = (k >= gj0) ? gj0 : k + 1;
     for (int r = lo + warp; r < n; r += NT / 32) {
       if (r == k) continue;
-      double2* Mr = M + (long long)r * ld;
-      const double2 m = Mr[k];
-      if (m.x == 0.0 && m.y == 0.0) continue;
+      T* Mr = M + (long long)r * ld;
+      const T m = Mr[k];
+      if (m.x == 0 && m.y == 0) continue;
       for (int c = k + 1 + lane; c < ncols; c += 32) {
-        const double2 u = prow[c];
-        double2 v = Mr[c];
+        const T u = prow[c];
+        T v = Mr[c];
         v.x -= m.x * u.x - m.y * u.y;
         v.y -= m.x * u.y + m.y * u.x;
         Mr[c] = v;
@@ -319,24 +321,25 @@ __global__ void __launch_bounds__(NT) gj_kernel(double2* W, long long wstride, i
 
 // R_C = I - 2 i eta X_bb and (optionally) H_C = -2 i eta X_bi from the
 // eliminated workspace, written to per-leaf storage with leading dims ldr/ldh.
-__global__ void extract_kernel(const double2* W, long long wstride, int ld, int n, int ni, int nb,
-                               double eta, int nbatch, double2* R, long long rstride, int ldr,
-                               double2* H, long long hstride, int ldh) {
+template <class T>
+__global__ void extract_kernel(const T* W, long long wstride, int ld, int n, int ni, int nb,
+                               double eta, int nbatch, T* R, long long rstride, int ldr,
+                               T* H, long long hstride, int ldh) {
   const int b = blockIdx.y;
   if (b >= nbatch) return;
   const int ncols_out = nb + (H ? ni : 0);
-  const double2* Wb = W + (long long)b * wstride;
+  const T* Wb = W + (long long)b * wstride;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nb * ncols_out;
        t += (long long)gridDim.x * blockDim.x) {
     const int jb = (int)(t / ncols_out), c = (int)(t % ncols_out);
-    const double2 v = Wb[(long long)(ni + jb) * ld + n + c];
+    const double2 v = cvt<double2>(Wb[(long long)(ni + jb) * ld + n + c]);
     // -2 i eta (v.x + i v.y) = 2 eta v.y - 2 i eta v.x
     double2 o = make_double2(2.0 * eta * v.y, -2.0 * eta * v.x);
     if (c < nb) {
       if (c == jb) o.x += 1.0;
-      R[(long long)b * rstride + (long long)jb * ldr + c] = o;
+      R[(long long)b * rstride + (long long)jb * ldr + c] = cvt<T>(o);
     } else {
-      H[(long long)b * hstride + (long long)jb * ldh + (c - nb)] = o;
+      H[(long long)b * hstride + (long long)jb * ldh + (c - nb)] = cvt<T>(o);
     }
   }
 }
@@ -344,19 +347,22 @@ __global__ void extract_kernel(const double2* W, long long wstride, int ld, int 
 // In-place S <- A S A^T on q x q segments of a batch of matrices.
 // mode 0: segment (row r, block f) = M[r][f q^2 + j]; mode 1: (col c, block f)
 // = M[f q^2 + j][c].  A = Q (trans = 0) or Q^{-T} (trans = 1; from Qi).
-__global__ void seg_kron_kernel(double2* M, long long mstride, int ld, int nrows, int ncols, int nbatch,
-                                const double* T, TableLayout tl, int trans, int mode) {
-  extern __shared__ double2 sm[];
+template <class T>
+__global__ void seg_kron_kernel(T* M, long long mstride, int ld, int nrows, int ncols, int nbatch,
+                                const double* tab, TableLayout tl, int trans, int mode) {
+  extern __shared__ __align__(16) unsigned char sk_smem[];
+  T* sm = reinterpret_cast<T*>(sk_smem);
+  using R_ = typename Real<T>::type;
   const int q = tl.q, q2 = q * q;
   const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double2* S = sm + warp * 2 * q2;
-  double2* T1 = S + q2;
-  const double* Am = T + (trans ? tl.Qi : tl.Q);
+  T* S = sm + warp * 2 * q2;
+  T* T1 = S + q2;
+  const double* Am = tab + (trans ? tl.Qi : tl.Q);
   const long long nseg_per = (mode == 0) ? (long long)nrows * (ncols / q2) : (long long)ncols * (nrows / q2);
   const long long nseg = nseg_per * nbatch;
   for (long long s = (long long)blockIdx.x * warps + warp; s < nseg; s += (long long)gridDim.x * warps) {
     const long long b = s / nseg_per, sl = s % nseg_per;
-    double2* base = M + b * mstride;
+    T* base = M + b * mstride;
     long long off;
     long long es;
     if (mode == 0) {
@@ -376,9 +382,9 @@ __global__ void seg_kron_kernel(double2* M, long long mstride, int ld, int nrows
     // T1[j2][a] = sum_j1 S[j2][j1] A(a, j1)
     for (int e = lane; e < q2; e += 32) {
       const int j2 = e / q, a = e % q;
-      double2 acc = make_double2(0.0, 0.0);
+      T acc = czero<T>();
       for (int j1 = 0; j1 < q; ++j1) {
-        const double av = trans ? Am[j1 * q + a] : Am[a * q + j1];
+        const R_ av = (R_)(trans ? Am[j1 * q + a] : Am[a * q + j1]);
         acc.x += S[j2 * q + j1].x * av;
         acc.y += S[j2 * q + j1].y * av;
       }
@@ -388,9 +394,9 @@ __global__ void seg_kron_kernel(double2* M, long long mstride, int ld, int nrows
     // out[bq][a] = sum_j2 A(bq, j2) T1[j2][a]
     for (int e = lane; e < q2; e += 32) {
       const int bq = e / q, a = e % q;
-      double2 acc = make_double2(0.0, 0.0);
+      T acc = czero<T>();
       for (int j2 = 0; j2 < q; ++j2) {
-        const double av = trans ? Am[j2 * q + bq] : Am[bq * q + j2];
+        const R_ av = (R_)(trans ? Am[j2 * q + bq] : Am[bq * q + j2]);
         acc.x += av * T1[j2 * q + a].x;
         acc.y += av * T1[j2 * q + a].y;
       }
@@ -443,7 +449,8 @@ __global__ void lambda_kernel(const double2* c, int ni, double2* lam) {
 }
 
 // B^leaf = R~^leaf[internal face rows][external face cols] for the leaves of a batch.
-__global__ void extract_b_kernel(const double2* Rt, long long rstride, int ldr, const int* leaf_ids,
+template <class T>
+__global__ void extract_b_kernel(const T* Rt, long long rstride, int ldr, const int* leaf_ids,
                                  int nbatch, int q, const uint8_t* int_mask, const long long* b_off,
                                  double2* B64, float2* B32) {
   const int b = blockIdx.y;
@@ -465,20 +472,21 @@ __global__ void extract_b_kernel(const double2* Rt, long long rstride, int ldr, 
        t += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(t / (next * q2)), c = (int)(t % (next * q2));
     const int rf = ifaces[r / q2], cf = efaces[c / q2];
-    const double2 v = Rt[(long long)b * rstride + (long long)(rf * q2 + r % q2) * ldr + cf * q2 + c % q2];
+    const T v = Rt[(long long)b * rstride + (long long)(rf * q2 + r % q2) * ldr + cf * q2 + c % q2];
     const long long o = off + (long long)r * ldb + c;
-    if (B64) B64[o] = v;
-    if (B32) B32[o] = make_float2((float)v.x, (float)v.y);
+    if (B64) B64[o] = cvt<double2>(v);
+    if (B32) B32[o] = cvt<float2>(v);
   }
 }
 
 // [I + D | I] for each cluster of a batch (row-major, ld = ldw); D couples
 // internal slot a (leaf alpha, face k) to the slots of beta = nbr(alpha, k)
 // through R~^beta's rows on face k^1.
-__global__ void assemble_cluster_kernel(double2* W, long long wstride, int ldw, int cl0, int nbatch,
+template <class T>
+__global__ void assemble_cluster_kernel(T* W, long long wstride, int ldw, int cl0, int nbatch,
                                         const int* cl_slot_begin, const int* slot_lf,
                                         const int* cl_leaf_begin, const int* cl_leaves,
-                                        const double2* Rt, long long rstride, int ldr, int leafpos0,
+                                        const T* Rt, long long rstride, int ldr, int leafpos0,
                                         GridDims g, int q) {
   const int b = blockIdx.y;
   if (b >= nbatch) return;
@@ -487,7 +495,7 @@ __global__ void assemble_cluster_kernel(double2* W, long long wstride, int ldw, 
   const int s0 = cl_slot_begin[c], ns = cl_slot_begin[c + 1] - s0;
   const int nint = ns * q2;
   const int lb = cl_leaf_begin[c], le = cl_leaf_begin[c + 1];
-  double2* Wb = W + (long long)b * wstride;
+  T* Wb = W + (long long)b * wstride;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nint * nint;
        t += (long long)gridDim.x * blockDim.x) {
     const int row = (int)(t / nint), col = (int)(t % nint);
@@ -496,22 +504,26 @@ __global__ void assemble_cluster_kernel(double2* W, long long wstride, int ldw, 
     const int lfa = slot_lf[s0 + sa], lfb = slot_lf[s0 + sb];
     const int alpha = lfa / 6, ka = lfa % 6;
     const int beta_b = lfb / 6, kb = lfb % 6;
-    double2 v = make_double2(row == col ? 1.0 : 0.0, 0.0);
+    T v = czero<T>();
+    if (row == col) v.x = 1;
     const int beta = g.neighbor(alpha, ka);
     if (beta == beta_b) {
       int pos = -1;
       for (int l = lb; l < le; ++l)
         if (cl_leaves[l] == beta) pos = l - leafpos0;
-      const double2 r = Rt[(long long)pos * rstride + (long long)((ka ^ 1) * q2 + ja) * ldr + kb * q2 + jb];
+      const T r = Rt[(long long)pos * rstride + (long long)((ka ^ 1) * q2 + ja) * ldr + kb * q2 + jb];
       v.x += r.x;
       v.y += r.y;
     }
     Wb[(long long)row * ldw + col] = v;
-    Wb[(long long)row * ldw + nint + col] = make_double2(row == col ? 1.0 : 0.0, 0.0);
+    T e = czero<T>();
+    if (row == col) e.x = 1;
+    Wb[(long long)row * ldw + nint + col] = e;
   }
 }
 
-__global__ void extract_kc_kernel(const double2* W, long long wstride, int ldw, int cl0, int nbatch,
+template <class T>
+__global__ void extract_kc_kernel(const T* W, long long wstride, int ldw, int cl0, int nbatch,
                                   const int* cl_slot_begin, const long long* kc_off, int q, double2* K64,
                                   float2* K32) {
   const int b = blockIdx.y;
@@ -523,16 +535,117 @@ __global__ void extract_kc_kernel(const double2* W, long long wstride, int ldw, 
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nint * nint;
        t += (long long)gridDim.x * blockDim.x) {
     const int row = (int)(t / nint), col = (int)(t % nint);
-    const double2 v = W[(long long)b * wstride + (long long)row * ldw + nint + col];
+    const T v = W[(long long)b * wstride + (long long)row * ldw + nint + col];
     const long long o = kc_off[c] + (long long)row * ldk + col;
-    if (K64) K64[o] = v;
-    if (K32) K32[o] = make_float2((float)v.x, (float)v.y);
+    if (K64) K64[o] = cvt<double2>(v);
+    if (K32) K32[o] = cvt<float2>(v);
+  }
+}
+
+// Right-hand-side columns [s; P^{-1} f] of the leaf systems of a batch (leaves
+// leaf0..leaf0+nbatch-1), one column per right-hand side at W[:, n + k].
+// P^{-1} maps a face's Gauss-point data F (q x q) to the Chebyshev face nodes:
+// Qi F Qi^T.
+__global__ void recover_rhs_kernel(double2* W, long long wstride, int ld, int leaf0, int nbatch, const double* tab,
+                                   TableLayout tl, const double2* s, const double2* f, int nrhs, long long nint,
+                                   long long nf) {
+  const int q = tl.q, q2 = q * q, n1 = tl.p - 2, ni = n1 * n1 * n1, nb = 6 * q2, n = ni + nb;
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  const int leaf = leaf0 + b;
+  const double* Qi = tab + tl.Qi;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * nrhs; t += gridDim.x * blockDim.x) {
+    const int r = t % n, k = t / n;
+    double2 v = make_double2(0.0, 0.0);
+    if (r < ni) {
+      if (s) v = s[k * nint + (long long)leaf * ni + r];
+    } else {
+      const int jb = r - ni, face = jb / q2, a = jb % q2, a1 = a % q, a2 = a / q;
+      const double2* F = f + k * nf + (long long)leaf * nb + (long long)face * q2;
+      for (int j2 = 0; j2 < q; ++j2) {
+        double2 row = make_double2(0.0, 0.0);
+        for (int j1 = 0; j1 < q; ++j1) row = cadd(row, cscale(F[j2 * q + j1], Qi[a1 * q + j1]));
+        v = cadd(v, cscale(row, Qi[a2 * q + j2]));
+      }
+    }
+    W[(long long)b * wstride + (long long)r * ld + n + k] = v;
+  }
+}
+
+__global__ void recover_extract_kernel(const double2* W, long long wstride, int ld, int n, int ni, int leaf0,
+                                       int nbatch, int nrhs, long long nint, double2* u) {
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ni * nrhs; t += gridDim.x * blockDim.x) {
+    const int r = t % ni, k = t / ni;
+    u[k * nint + (long long)(leaf0 + b) * ni + r] = W[(long long)b * wstride + (long long)r * ld + n + k];
+  }
+}
+
+// FP16 copy of one complex-float row with one FP32 scale: the row is divided by
+// s = max(|re|, |im|) over the row before rounding to half precision.
+__device__ __forceinline__ void quantize_row(const float2* src, __half2* dst, int ncols, float* scale, int lane) {
+  float m = 0.f;
+  for (int c = lane; c < ncols; c += 32) m = fmaxf(m, fmaxf(fabsf(src[c].x), fabsf(src[c].y)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float s = (m > 0.f) ? m : 1.f;
+  const float inv = 1.f / s;
+  for (int c = lane; c < ncols; c += 32) dst[c] = __floats2half2_rn(src[c].x * inv, src[c].y * inv);
+  if (lane == 0) *scale = s;
+}
+
+// rows of every K_c; global row gr = slot * q^2 + j
+__global__ void quantize_kc_kernel(const float2* K32, __half2* K16, float* kscale, const int* slot_cluster,
+                                   const int* cl_slot_begin, const long long* kc_off, int q2, long long nrows) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long gr = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); gr < nrows; gr += warps) {
+    const int slot = (int)(gr / q2);
+    const int c = slot_cluster[slot];
+    const int s0 = cl_slot_begin[c];
+    const int nint = (cl_slot_begin[c + 1] - s0) * q2;
+    const long long off = kc_off[c] + (gr - (long long)s0 * q2) * rup4(nint);
+    quantize_row(K32 + off, K16 + off, nint, kscale + gr, lane);
+  }
+}
+
+// rows of every B^leaf; row index (leaf*6 + face)*q^2 + j for internal faces
+__global__ void quantize_b_kernel(const float2* B32, __half2* B16, float* bscale, const uint8_t* int_mask,
+                                  const long long* b_off, int q2, long long nrows) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long gr = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); gr < nrows; gr += warps) {
+    const int leaf = (int)(gr / (6 * q2));
+    const int face = (int)((gr / q2) % 6);
+    const int j = (int)(gr % q2);
+    const unsigned mask = int_mask[leaf];
+    if (!(mask & (1u << face))) continue;
+    const int rb = __popc(mask & ((1u << face) - 1u));
+    const int ncols = (6 - __popc(mask)) * q2;
+    const long long off = b_off[leaf] + (long long)(rb * q2 + j) * rup4(ncols);
+    quantize_row(B32 + off, B16 + off, ncols, bscale + gr, lane);
   }
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
+int build_precond_fp16(hps_handle* h, cudaStream_t st) {
+  const int q2 = h->q * h->q;
+  const long long krows = (long long)h->ct.nslots * q2;
+  const long long brows = (long long)h->nl * 6 * q2;
+  if (krows > 0) {
+    quantize_kc_kernel<<<h->nsm * 8, 256, 0, st>>>(h->Kc32, h->Kc16, h->Kc16s, h->dct.slot_cluster,
+                                                    h->dct.cl_slot_begin, h->dct.cl_kc_off, q2, krows);
+    HPS_CUDA_TRY(cudaGetLastError());
+  }
+  quantize_b_kernel<<<h->nsm * 8, 256, 0, st>>>(h->B32, h->B16, h->B16s, h->dct.int_mask, h->dct.b_off, q2, brows);
+  HPS_CUDA_TRY(cudaGetLastError());
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  return HPS_OK;
+}
+
 cudaError_t launch_tables(double* tables, const TableLayout& tl, double hx, double hy, double hz,
                           cudaStream_t st) {
   tables_kernel<<<1, 32, 0, st>>>(tables, tl, hx, hy, hz);
@@ -554,23 +667,25 @@ namespace {
 
 constexpr int kGjThreads = 512;
 
-cudaError_t run_gj(double2* W, long long wstride, int ld, int n, int ncols, int gj0, int nbatch, int* status,
+template <class T>
+cudaError_t run_gj(T* W, long long wstride, int ld, int n, int ncols, int gj0, int nbatch, int* status,
                    cudaStream_t st) {
-  const size_t smem = (size_t)ncols * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(gj_kernel<kGjThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = (size_t)ncols * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(gj_kernel<T, kGjThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  gj_kernel<kGjThreads><<<nbatch, kGjThreads, smem, st>>>(W, wstride, ld, n, ncols, gj0, nbatch, status);
+  gj_kernel<T, kGjThreads><<<nbatch, kGjThreads, smem, st>>>(W, wstride, ld, n, ncols, gj0, nbatch, status);
   return cudaGetLastError();
 }
 
-cudaError_t run_seg_kron(double2* M, long long mstride, int ld, int nrows, int ncols, int nbatch,
-                         const double* T, const TableLayout& tl, int trans, int mode, int nsm, cudaStream_t st) {
+template <class T>
+cudaError_t run_seg_kron(T* M, long long mstride, int ld, int nrows, int ncols, int nbatch,
+                         const double* tables, const TableLayout& tl, int trans, int mode, int nsm, cudaStream_t st) {
   const int q2 = tl.q * tl.q;
-  const size_t smem = 8 * 2 * q2 * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(seg_kron_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = 8 * 2 * q2 * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(seg_kron_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  seg_kron_kernel<<<nsm * 8, 256, smem, st>>>(M, mstride, ld, nrows, ncols, nbatch, T, tl, trans, mode);
+  seg_kron_kernel<T><<<nsm * 8, 256, smem, st>>>(M, mstride, ld, nrows, ncols, nbatch, tables, tl, trans, mode);
   return cudaGetLastError();
 }
 
@@ -589,17 +704,54 @@ int check_status(int* d_status, cudaStream_t st, const char* what) {
 size_t workspace_budget(const hps_handle* h) {
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
-  size_t cap = (size_t)24 << 30;
-  size_t b = fr / 3;
-  return b < cap ? b : cap;
+  return std::min(workspace_cap(h), fr / 3);
 }
 
 }  // namespace
 
-int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
-  const int n = h->n, ni = h->ni, nb = h->nb;
-  const int ncols = n + nb + ni;
-  const int ld = ncols;
+// Cap on the transient setup workspace: 24 GiB, the remaining HBM budget of
+// the handle when one is set, (setup also keeps it under a third of the free device memory).
+size_t workspace_cap(const hps_handle* h) {
+  size_t cap = (size_t)24 << 30;
+  if (h->opt.hbm_budget) {
+    const size_t rest = h->opt.hbm_budget > h->bytes ? h->opt.hbm_budget - h->bytes : 0;
+    cap = std::min(cap, rest);
+  }
+  return cap;
+}
+
+size_t exact_maps_workspace(const hps_handle* h, size_t budget, int* nbatch_out) {
+  const long long per = (long long)h->n * (h->n + h->nb + h->ni) * (long long)sizeof(double2);
+  int nbatch = (int)std::min<long long>((long long)h->nl, std::max<long long>(1, (long long)(budget / per)));
+  nbatch = std::min(nbatch, 4 * h->nsm);
+  if (nbatch_out) *nbatch_out = nbatch;
+  return (size_t)per * nbatch;
+}
+
+size_t precond_workspace(const hps_handle* h, size_t budget, int* cb_out) {
+  const ClusterTables& ct = h->ct;
+  const int q2 = h->q * h->q;
+  int max_int = 0, max_leaves = 0;
+  for (int c = 0; c < ct.ncl; ++c) {
+    max_int = std::max(max_int, (ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2);
+    max_leaves = std::max(max_leaves, ct.cl_leaf_begin[c + 1] - ct.cl_leaf_begin[c]);
+  }
+  const long long wl_stride = (long long)h->n * (h->n + h->nb);
+  const int ldw = std::max(2, 2 * max_int);
+  const long long wc_stride = (long long)std::max(1, max_int) * ldw;
+  const size_t per_cluster =
+      ((size_t)wl_stride * max_leaves + (size_t)h->nb * h->ldR * max_leaves + (size_t)wc_stride) * sizeof(double2);
+  int cb = (int)std::min<size_t>((size_t)std::max(1, ct.ncl), std::max<size_t>(1, budget / per_cluster));
+  cb = std::min(cb, std::max(1, 2 * h->nsm));
+  if (cb_out) *cb_out = cb;
+  return per_cluster * cb;
+}
+
+// Interior values of the leaf solutions u^tau = A^{tau,-1} [s^tau; P^{-1} f^tau]
+// (eq. (leaf)), by FP64 elimination of each leaf system with nrhs extra columns.
+int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, cudaStream_t st) {
+  const int n = h->n, ni = h->ni;
+  const int ncols = n + nrhs, ld = ncols;
   const long long wstride = (long long)n * ld;
   const size_t per = (size_t)wstride * sizeof(double2);
   int nbatch = (int)std::min<size_t>((size_t)h->nl, std::max<size_t>(1, workspace_budget(h) / per));
@@ -615,15 +767,54 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
     auto body = [&]() -> int {
       HPS_CUDA_TRY(cudaMemsetAsync(W, 0, per * nbt, st));
       dim3 ga((n + 127) / 128, nbt);
-      assemble_kernel<<<ga, 128, 0, st>>>(W, wstride, ld, nullptr, l0, nbt, h->tables, h->tl, h->eta, cdiag,
-                                         nullptr, 1);
+      assemble_kernel<double2><<<ga, 128, 0, st>>>(W, wstride, ld, nullptr, l0, nbt, h->tables, h->tl, h->eta,
+                                                  h->cdiag, nullptr, 0);
+      HPS_CUDA_TRY(cudaGetLastError());
+      recover_rhs_kernel<<<dim3(32, nbt), 128, 0, st>>>(W, wstride, ld, l0, nbt, h->tables, h->tl, s, f, nrhs,
+                                                         h->nint, h->nf);
+      HPS_CUDA_TRY(cudaGetLastError());
+      HPS_CUDA_TRY(run_gj(W, wstride, ld, n, ncols, 0, nbt, d_status, st));
+      recover_extract_kernel<<<dim3(32, nbt), 128, 0, st>>>(W, wstride, ld, n, ni, l0, nbt, nrhs, h->nint, u);
+      HPS_CUDA_TRY(cudaGetLastError());
+      return HPS_OK;
+    };
+    rc = body();
+  }
+  if (rc == HPS_OK) rc = check_status(d_status, st, "leaf solution recovery");
+  cudaStreamSynchronize(st);
+  cudaFree(W);
+  cudaFree(d_status);
+  return rc;
+}
+
+int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+  const int n = h->n, ni = h->ni, nb = h->nb;
+  const int ncols = n + nb + ni;
+  const int ld = ncols;
+  const long long wstride = (long long)n * ld;
+  const size_t per = (size_t)wstride * sizeof(double2);
+  int nbatch = 1;
+  exact_maps_workspace(h, workspace_budget(h), &nbatch);
+  double2* W = nullptr;
+  int* d_status = nullptr;
+  HPS_CUDA_TRY(cudaMalloc(&W, per * nbatch));
+  HPS_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
+  HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  int rc = HPS_OK;
+  for (int l0 = 0; l0 < h->nl && rc == HPS_OK; l0 += nbatch) {
+    const int nbt = std::min(nbatch, h->nl - l0);
+    auto body = [&]() -> int {
+      HPS_CUDA_TRY(cudaMemsetAsync(W, 0, per * nbt, st));
+      dim3 ga((n + 127) / 128, nbt);
+      assemble_kernel<double2><<<ga, 128, 0, st>>>(W, wstride, ld, nullptr, l0, nbt, h->tables, h->tl, h->eta,
+                                                  cdiag, nullptr, 2);
       HPS_CUDA_TRY(cudaGetLastError());
       HPS_CUDA_TRY(run_gj(W, wstride, ld, n, ncols, ni, nbt, d_status, st));
       double2* Rb = h->R64 + (long long)l0 * nb * h->ldR;
       double2* Hb = h->H64 + (long long)l0 * nb * h->ldH;
       dim3 ge(256, nbt);
-      extract_kernel<<<ge, 256, 0, st>>>(W, wstride, ld, n, ni, nb, h->eta, nbt, Rb, (long long)nb * h->ldR,
-                                         h->ldR, Hb, (long long)nb * h->ldH, h->ldH);
+      extract_kernel<double2><<<ge, 256, 0, st>>>(W, wstride, ld, n, ni, nb, h->eta, nbt, Rb,
+                                                  (long long)nb * h->ldR, h->ldR, Hb, (long long)nb * h->ldH, h->ldH);
       HPS_CUDA_TRY(cudaGetLastError());
       // R = P (R_C P^{-1}): rows by Q^{-T} (.) Q^{-1}, then columns by Q (.) Q^T.
       HPS_CUDA_TRY(run_seg_kron(Rb, (long long)nb * h->ldR, h->ldR, nb, nb, nbt, h->tables, h->tl, 1, 0, h->nsm, st));
@@ -699,16 +890,97 @@ void build_cluster_tables(hps_handle* h, int width) {
   ct.b_elems = off;
 }
 
-int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+// The cluster blocks built with elimination in T: complex double when the FP64
+// form is kept, complex float otherwise (the FP32 elimination gives the
+// boundary block of the inverse to ~2e-7, far below what a preconditioner
+// needs, at the FP32 rate).
+template <class T>
+int build_precond_blocks(hps_handle* h, const double2* cdiag, const int* d_cl_leaf_begin, const int* d_cl_leaves,
+                         cudaStream_t st) {
   ClusterTables& ct = h->ct;
   const int n = h->n, ni = h->ni, nb = h->nb, q = h->q, q2 = q * q;
+  int max_int = 0, max_leaves = 0;
+  for (int c = 0; c < ct.ncl; ++c) {
+    max_int = std::max(max_int, (ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2);
+    max_leaves = std::max(max_leaves, ct.cl_leaf_begin[c + 1] - ct.cl_leaf_begin[c]);
+  }
+  const int ncols_l = n + nb, ld_l = ncols_l;
+  const long long wl_stride = (long long)n * ld_l;
+  const int ldw = std::max(2, 2 * max_int);
+  const long long wc_stride = (long long)std::max(1, max_int) * ldw;
+  int cb = 1;
+  precond_workspace(h, workspace_budget(h), &cb);
+  T *Wl = nullptr, *Rt = nullptr, *Wc = nullptr;
+  int* d_status = nullptr;
+  HPS_CUDA_TRY(cudaMalloc(&Wl, (size_t)wl_stride * max_leaves * cb * sizeof(T)));
+  HPS_CUDA_TRY(cudaMalloc(&Rt, (size_t)nb * h->ldR * max_leaves * cb * sizeof(T)));
+  HPS_CUDA_TRY(cudaMalloc(&Wc, (size_t)wc_stride * cb * sizeof(T)));
+  HPS_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
+  HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  GridDims gd{h->nx, h->ny, h->nz};
+  int rc = HPS_OK;
+  for (int c0 = 0; c0 < ct.ncl && rc == HPS_OK; c0 += cb) {
+    const int nc = std::min(cb, ct.ncl - c0);
+    const int lb = ct.cl_leaf_begin[c0], le = ct.cl_leaf_begin[c0 + nc];
+    const int nlb = le - lb;
+    const int* leaf_ids = d_cl_leaves + lb;
+    auto body = [&]() -> int {
+      HPS_CUDA_TRY(cudaMemsetAsync(Wl, 0, (size_t)wl_stride * nlb * sizeof(T), st));
+      dim3 ga((n + 127) / 128, nlb);
+      assemble_kernel<T><<<ga, 128, 0, st>>>(Wl, wl_stride, ld_l, leaf_ids, 0, nlb, h->tables, h->tl, h->eta,
+                                             cdiag, h->lambda, 1);
+      HPS_CUDA_TRY(cudaGetLastError());
+      HPS_CUDA_TRY(run_gj(Wl, wl_stride, ld_l, n, ncols_l, ni, nlb, d_status, st));
+      dim3 ge(256, nlb);
+      extract_kernel<T><<<ge, 256, 0, st>>>(Wl, wl_stride, ld_l, n, ni, nb, h->eta, nlb, Rt, (long long)nb * h->ldR,
+                                            h->ldR, nullptr, 0, 0);
+      HPS_CUDA_TRY(cudaGetLastError());
+      HPS_CUDA_TRY(run_seg_kron(Rt, (long long)nb * h->ldR, h->ldR, nb, nb, nlb, h->tables, h->tl, 1, 0, h->nsm, st));
+      HPS_CUDA_TRY(run_seg_kron(Rt, (long long)nb * h->ldR, h->ldR, nb, nb, nlb, h->tables, h->tl, 0, 1, h->nsm, st));
+      extract_b_kernel<T><<<dim3(64, nlb), 256, 0, st>>>(Rt, (long long)nb * h->ldR, h->ldR, leaf_ids, nlb, q,
+                                                         h->dct.int_mask, h->dct.b_off, h->B64, h->B32);
+      HPS_CUDA_TRY(cudaGetLastError());
+      assemble_cluster_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
+                                                                h->dct.slot_lf, d_cl_leaf_begin, d_cl_leaves, Rt,
+                                                                (long long)nb * h->ldR, h->ldR, lb, gd, q);
+      HPS_CUDA_TRY(cudaGetLastError());
+      // clusters of one size are eliminated in one launch
+      int cstart = c0;
+      while (cstart < c0 + nc) {
+        const int sz = (ct.cl_slot_begin[cstart + 1] - ct.cl_slot_begin[cstart]) * q2;
+        int cend = cstart + 1;
+        while (cend < c0 + nc && (ct.cl_slot_begin[cend + 1] - ct.cl_slot_begin[cend]) * q2 == sz) ++cend;
+        if (sz > 0)
+          HPS_CUDA_TRY(run_gj(Wc + (long long)(cstart - c0) * wc_stride, wc_stride, ldw, sz, 2 * sz, 0, cend - cstart,
+                              d_status, st));
+        cstart = cend;
+      }
+      extract_kc_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
+                                                          h->dct.cl_kc_off, q, h->Kc64, h->Kc32);
+      HPS_CUDA_TRY(cudaGetLastError());
+      return HPS_OK;
+    };
+    rc = body();
+  }
+  if (rc == HPS_OK) rc = check_status(d_status, st, "preconditioner blocks");
+  cudaStreamSynchronize(st);
+  cudaFree(Wl);
+  cudaFree(Rt);
+  cudaFree(Wc);
+  cudaFree(d_status);
+  return rc;
+}
+
+int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+  ClusterTables& ct = h->ct;
   // device copies of the tables
   auto up = [&](auto*& dst, const auto& vec) -> int {
-    using T = std::remove_reference_t<decltype(vec[0])>;
-    const size_t bytes = std::max<size_t>(1, vec.size()) * sizeof(T);
+    using E = std::remove_reference_t<decltype(vec[0])>;
+    const size_t bytes = std::max<size_t>(1, vec.size()) * sizeof(E);
     HPS_CUDA_TRY(cudaMalloc((void**)&dst, bytes));
     h->bytes += bytes;
-    if (!vec.empty()) HPS_CUDA_TRY(cudaMemcpyAsync((void*)dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    if (!vec.empty())
+      HPS_CUDA_TRY(cudaMemcpyAsync((void*)dst, vec.data(), vec.size() * sizeof(E), cudaMemcpyHostToDevice, st));
     return HPS_OK;
   };
   int rc;
@@ -727,82 +999,11 @@ int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
                                cudaMemcpyHostToDevice, st));
   HPS_CUDA_TRY(cudaMemcpyAsync(d_cl_leaves, ct.cl_leaves.data(), ct.cl_leaves.size() * sizeof(int),
                                cudaMemcpyHostToDevice, st));
-
-  lambda_kernel<<<h->nl, 256, 0, st>>>(cdiag, ni, h->lambda);
+  lambda_kernel<<<h->nl, 256, 0, st>>>(cdiag, h->ni, h->lambda);
   HPS_CUDA_TRY(cudaGetLastError());
-
-  // batch sizes: clusters per batch limited by the two workspaces
-  int max_int = 0, max_leaves = 0;
-  for (int c = 0; c < ct.ncl; ++c) {
-    max_int = std::max(max_int, (ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2);
-    max_leaves = std::max(max_leaves, ct.cl_leaf_begin[c + 1] - ct.cl_leaf_begin[c]);
-  }
-  const int ncols_l = n + nb, ld_l = ncols_l;
-  const long long wl_stride = (long long)n * ld_l;
-  const int ldw = std::max(2, 2 * max_int);
-  const long long wc_stride = (long long)std::max(1, max_int) * ldw;
-  const size_t per_cluster = ((size_t)wl_stride * max_leaves + (size_t)nb * h->ldR * max_leaves + (size_t)wc_stride) *
-                             sizeof(double2);
-  int cb = (int)std::min<size_t>((size_t)ct.ncl, std::max<size_t>(1, workspace_budget(h) / per_cluster));
-  cb = std::min(cb, std::max(1, 2 * h->nsm));
-  double2 *Wl = nullptr, *Rt = nullptr, *Wc = nullptr;
-  int* d_status = nullptr;
-  int* d_leafids = nullptr;
-  HPS_CUDA_TRY(cudaMalloc(&Wl, (size_t)wl_stride * max_leaves * cb * sizeof(double2)));
-  HPS_CUDA_TRY(cudaMalloc(&Rt, (size_t)nb * h->ldR * max_leaves * cb * sizeof(double2)));
-  HPS_CUDA_TRY(cudaMalloc(&Wc, (size_t)wc_stride * cb * sizeof(double2)));
-  HPS_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
-  HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
-  GridDims gd{h->nx, h->ny, h->nz};
-  for (int c0 = 0; c0 < ct.ncl && rc == HPS_OK; c0 += cb) {
-    const int nc = std::min(cb, ct.ncl - c0);
-    const int lb = ct.cl_leaf_begin[c0], le = ct.cl_leaf_begin[c0 + nc];
-    const int nlb = le - lb;
-    const int* leaf_ids = d_cl_leaves + lb;
-    auto body = [&]() -> int {
-      HPS_CUDA_TRY(cudaMemsetAsync(Wl, 0, (size_t)wl_stride * nlb * sizeof(double2), st));
-      dim3 ga((n + 127) / 128, nlb);
-      assemble_kernel<<<ga, 128, 0, st>>>(Wl, wl_stride, ld_l, leaf_ids, 0, nlb, h->tables, h->tl, h->eta,
-                                          cdiag, h->lambda, 0);
-      HPS_CUDA_TRY(cudaGetLastError());
-      HPS_CUDA_TRY(run_gj(Wl, wl_stride, ld_l, n, ncols_l, ni, nlb, d_status, st));
-      dim3 ge(256, nlb);
-      extract_kernel<<<ge, 256, 0, st>>>(Wl, wl_stride, ld_l, n, ni, nb, h->eta, nlb, Rt, (long long)nb * h->ldR,
-                                         h->ldR, nullptr, 0, 0);
-      HPS_CUDA_TRY(cudaGetLastError());
-      HPS_CUDA_TRY(run_seg_kron(Rt, (long long)nb * h->ldR, h->ldR, nb, nb, nlb, h->tables, h->tl, 1, 0, h->nsm, st));
-      HPS_CUDA_TRY(run_seg_kron(Rt, (long long)nb * h->ldR, h->ldR, nb, nb, nlb, h->tables, h->tl, 0, 1, h->nsm, st));
-      extract_b_kernel<<<dim3(64, nlb), 256, 0, st>>>(Rt, (long long)nb * h->ldR, h->ldR, leaf_ids, nlb, q,
-                                                      h->dct.int_mask, h->dct.b_off, h->B64, h->B32);
-      HPS_CUDA_TRY(cudaGetLastError());
-      assemble_cluster_kernel<<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
-                                                             h->dct.slot_lf, d_cl_leaf_begin, d_cl_leaves, Rt,
-                                                             (long long)nb * h->ldR, h->ldR, lb, gd, q);
-      HPS_CUDA_TRY(cudaGetLastError());
-      // all clusters of a batch share max_int only when they have equal size; run per distinct size
-      int cstart = c0;
-      while (cstart < c0 + nc) {
-        const int sz = (ct.cl_slot_begin[cstart + 1] - ct.cl_slot_begin[cstart]) * q2;
-        int cend = cstart + 1;
-        while (cend < c0 + nc && (ct.cl_slot_begin[cend + 1] - ct.cl_slot_begin[cend]) * q2 == sz) ++cend;
-        if (sz > 0)
-          HPS_CUDA_TRY(run_gj(Wc + (long long)(cstart - c0) * wc_stride, wc_stride, ldw, sz, 2 * sz, 0, cend - cstart,
-                              d_status, st));
-        cstart = cend;
-      }
-      extract_kc_kernel<<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
-                                                       h->dct.cl_kc_off, q, h->Kc64, h->Kc32);
-      HPS_CUDA_TRY(cudaGetLastError());
-      return HPS_OK;
-    };
-    rc = body();
-  }
-  if (rc == HPS_OK) rc = check_status(d_status, st, "preconditioner blocks");
+  rc = h->Kc64 ? build_precond_blocks<double2>(h, cdiag, d_cl_leaf_begin, d_cl_leaves, st)
+               : build_precond_blocks<float2>(h, cdiag, d_cl_leaf_begin, d_cl_leaves, st);
   cudaStreamSynchronize(st);
-  cudaFree(Wl);
-  cudaFree(Rt);
-  cudaFree(Wc);
-  cudaFree(d_status);
   cudaFree(d_cl_leaf_begin);
   cudaFree(d_cl_leaves);
   return rc;

@@ -61,3 +61,5 @@ def test_algorithmic_bytes_formulas():
     assert bench.apply_bytes(16, 8, 8, 8, 16) == rows * 384 * 8 + 16 ** 3 * 384 * 32
     kb, bb = bench.precond_bytes(16, 8, 8, 8)
     assert kb == 512 * 1536 * 1536 * 8 + 512 * 1536 * 16
+    kb16, _ = bench.precond_bytes(16, 8, 4, 8, in_bytes=16, scale_bytes=4)
+    assert kb16 == 512 * 1536 * (1536 * 4 + 4) + 512 * 1536 * 16

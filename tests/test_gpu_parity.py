@@ -96,20 +96,60 @@ def test_precond_matches_oracle(ragged, nrhs):
     assert rel(z32, ref32) < 2e-5
 
 
+def test_precond_fp16_blocks_close_to_oracle(ragged):
+    """FP16 copies of the cluster blocks (one FP32 scale per row, as used by the mixed
+    solve): half precision (2^-11) per entry, amplified by the sum over a row."""
+    w, oc, solver, _ = ragged
+    r = _rand(oc.grid.nf, 31, 1)[0].astype(np.complex64)
+    ref = oc.M(r.astype(np.complex128))
+    z = solver.precond(torch.from_numpy(r).cuda(), fp16_blocks=True).cpu().numpy()
+    assert rel(z, ref) < 5e-3
+
+
+def test_mixed_only_handle_builds_fp32_preconditioner(ragged):
+    """Without the FP64 form the cluster blocks come from FP32 elimination; they stay
+    within FP32 accuracy of the oracle's, and the mixed solve still meets its bar."""
+    w, oc, _, (xi, xf, b, s, t) = ragged
+    solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",))
+    try:
+        r = _rand(oc.grid.nf, 41, 1)[0].astype(np.complex64)
+        z = solver.precond(torch.from_numpy(r).cuda()).cpu().numpy()
+        assert rel(z, oc.M(r.astype(np.complex128))) < 1e-4
+        f, info = solver.solve(s=torch.from_numpy(s.reshape(-1)).cuda(), t=torch.from_numpy(t.reshape(-1)).cuda(),
+                               tol=1e-8, form="mixed")
+        assert info["converged"] and rel(f.cpu().numpy(), oc.solve()) < 1e-6
+    finally:
+        solver.close()
+
+
 def test_rhs_matches_oracle(ragged):
     w, oc, solver, (xi, xf, b, s, t) = ragged
     bg = solver.rhs(torch.from_numpy(s.reshape(-1)).cuda(), torch.from_numpy(t.reshape(-1)).cuda())
     assert rel(bg.cpu().numpy(), oc.rhs()) < 1e-11
 
 
-@pytest.mark.parametrize("form,tol,bar", [("fp64", 1e-12, 1e-10), ("mixed", 1e-8, 1e-6)])
+@pytest.mark.parametrize("form,tol,bar", [("fp64", 1e-12, 1e-10), ("mixed", 1e-8, 1e-6), ("mixed", 1e-12, 1e-10)])
 def test_solve_matches_oracle(ragged, form, tol, bar):
+    """The mixed form restarts from the FP64 true residual, so at a tight tolerance it
+    reaches the FP64 bar as well."""
     w, oc, solver, (xi, xf, b, s, t) = ragged
     f_ref = oc.solve()
     f, info = solver.solve(s=torch.from_numpy(s.reshape(-1)).cuda(), t=torch.from_numpy(t.reshape(-1)).cuda(),
                            tol=tol, form=form)
     assert info["converged"], info
     assert rel(f.cpu().numpy(), f_ref) < bar, info
+
+
+def test_recover_interior_matches_oracle(ragged):
+    """u = A^{-1}[s; P^{-1} f] per leaf from the GPU face solution, against the oracle's
+    recovery from its own solution and against the manufactured u."""
+    w, oc, solver, (xi, xf, b, s, t) = ragged
+    sd = torch.from_numpy(s.reshape(-1)).cuda()
+    f, info = solver.solve(s=sd, t=torch.from_numpy(t.reshape(-1)).cuda(), tol=1e-12, form="fp64")
+    u = solver.recover(f, s=sd).cpu().numpy().reshape(oc.grid.nleaves, -1)
+    ref = O.recover_interior(oc.grid, w.kappa, w.eta, oc.b, oc.s[0], oc.solve())
+    assert rel(u, ref) < 1e-10
+    assert rel(u, w.meta["u"](oc.xi)) < 1e-2
 
 
 def test_solve_host_buffers_match_device_buffers(ragged):
@@ -164,12 +204,13 @@ def plane_wave_4cubed():
 
 
 @pytest.mark.parametrize("form,bar", [("fp64", 1e-10), ("mixed", 1e-6)])
-def test_plane_wave_4cubed_solve(plane_wave_4cubed, form, bar):
+@pytest.mark.parametrize("precond", [True, False])
+def test_plane_wave_4cubed_solve(plane_wave_4cubed, form, bar, precond):
     """4^3 leaves, p = 8, kappa = eta = 10, plane wave, GMRES(50) with 2x2x2 clusters."""
     w, oc, solver, t = plane_wave_4cubed
     f_ref = oc.solve()
     f, info = solver.solve(t=torch.from_numpy(t.reshape(-1)).cuda(), tol=w.tol if form == "fp64" else 1e-8,
-                           form=form)
+                           form=form, precond=precond)
     assert info["converged"], info
     f = f.cpu().numpy()
     assert rel(f, f_ref) < bar, info
@@ -188,7 +229,7 @@ def bump_4cubed():
     solver.close()
 
 
-@pytest.mark.parametrize("form,tol,bar", [("fp64", 1e-11, 1e-10), ("mixed", 1e-7, 1e-6)])
+@pytest.mark.parametrize("form,tol,bar", [("fp64", 1e-11, 1e-10), ("mixed", 1e-7, 1e-6), ("mixed", 1e-11, 1e-10)])
 def test_bump_scaled_solve(bump_4cubed, form, tol, bar):
     """The variable-coefficient workload (p = 10, kappa = 40, Gaussian bump and source) on 4^3 leaves."""
     w, oc, solver, s = bump_4cubed

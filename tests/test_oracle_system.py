@@ -66,6 +66,20 @@ def test_manufactured_solution_converges():
         assert b_ < a / 10
 
 
+def test_recovered_interior_solution_converges():
+    """u = A^{-1}[s; P^{-1} f] from the face solution reproduces the manufactured u at
+    the interior nodes, spectrally in p."""
+    errs = []
+    for p in (6, 8, 10):
+        w = W.manufactured(L=2, p=p, kappa=8.0)
+        grid, prob, rhs, (xi, xf, nrm, b, s, t) = _setup(w)
+        f = np.linalg.solve(O.dense_face_matrix(grid, prob.R), rhs)
+        u = O.recover_interior(grid, w.kappa, w.eta, b, s[0], f)
+        errs.append(O.relative_error(u, w.meta["u"](xi)))
+    assert errs[-1] < 1e-4
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10
+
+
 def test_dense_solve_matches_gmres_and_preconditioned_gmres():
     w = W.manufactured(L=2, p=6, kappa=12.0)
     w.ny = 2

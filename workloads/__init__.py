@@ -263,20 +263,23 @@ def large_32cubed(L=32, p=10, kappa=200.0):
                     meta={"modes": modes.tolist()})
 
 
-def serving_stream(n=500, rate=20.0, seed=7):
-    """Request stream: Poisson arrivals (mean `rate`/s); per request L in 8..24,
-    p in {8, 10, 12}, kappa ~ U[20, 120], 3-8 Gaussian bumps, 1-16 Gaussian sources."""
+def serving_stream(n=500, rate=20.0, seed=7, L_range=(8, 24), p_choices=(8, 10, 12), kappa_range=(20.0, 120.0),
+                   max_sources=16):
+    """Request stream: Poisson arrivals (mean `rate`/s); per request L in L_range (inclusive),
+    p in p_choices, kappa ~ U[kappa_range], 3-8 Gaussian bumps, 1-max_sources Gaussian sources
+    (width 0.02).  The defaults are the serving workload; smaller ranges give a scaled stream
+    with the same recipe."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for i in range(n):
         t += rng.exponential(1.0 / rate)
-        L = int(rng.integers(8, 25))
-        p = int(rng.choice([8, 10, 12]))
-        kappa = float(rng.uniform(20.0, 120.0))
+        L = int(rng.integers(L_range[0], L_range[1] + 1))
+        p = int(rng.choice(list(p_choices)))
+        kappa = float(rng.uniform(kappa_range[0], kappa_range[1]))
         nb = int(rng.integers(3, 9))
         b, meta = gaussian_bumps(rng, nb)
-        ns = int(rng.integers(1, 17))
+        ns = int(rng.integers(1, max_sources + 1))
         xs = rng.uniform(0.1, 0.9, size=(ns, 3))
         s = [gaussian(xs[j], width=0.02) for j in range(ns)]
         w = Workload(name=f"request_{i}", nx=L, ny=L, nz=L, p=p, kappa=kappa, eta=kappa, b=b,
