@@ -30,7 +30,7 @@ __all__ = [
     "chebyshev_lobatto", "chebyshev_diff", "gauss_legendre", "lagrange_matrix",
     "LeafLayout", "Grid", "leaf_matrix", "leaf_maps", "face_interp",
     "leaf_iti", "interior_nodes", "face_nodes", "face_normals",
-    "homogenized_lambda", "leaf_incoming_op", "leaf_outgoing_op",
+    "homogenized_lambda", "binned_lambdas", "leaf_incoming_op", "leaf_outgoing_op",
 ]
 
 # Face k in 0..5 is -x, +x, -y, +y, -z, +z (Sec. 2.1, "I_1 the left ...").
@@ -360,3 +360,22 @@ def homogenized_lambda(cdiag):
     re = 0.5 * (c.real.max() + c.real.min())
     im = 0.5 * (c.imag.max() + c.imag.min())
     return re + 1j * im
+
+
+def binned_lambdas(lams, delta):
+    """Homogenized constants rounded so that leaves with nearly the same medium share one solver.
+
+    Sec. 4.1 remarks that the local approximate solver can be reused for
+    leaves whose medium is roughly the same.  Here "roughly the same" is a
+    bin: with w = delta * max_tau |lambda^tau|, each lambda^tau is replaced by
+    the nearest multiple of w, real and imaginary parts separately (ties to
+    even).  delta = 0 keeps every lambda^tau as it is.  Leaves with equal
+    binned values get bitwise equal homogenized maps.
+    """
+    lams = np.asarray(lams, dtype=np.complex128)
+    if delta <= 0 or lams.size == 0:
+        return lams.copy()
+    w = float(delta) * float(np.abs(lams).max())
+    if w == 0.0:
+        return lams.copy()
+    return w * np.rint(lams.real / w) + 1j * (w * np.rint(lams.imag / w))

@@ -27,7 +27,7 @@ cluster acting as given impedance data:  z_c = (I + Pi_c R~)^{-1} r_c.
 import numpy as np
 
 from .discretization import (
-    Grid, LeafLayout, homogenized_lambda, leaf_iti,
+    Grid, LeafLayout, binned_lambdas, homogenized_lambda, leaf_iti,
 )
 
 __all__ = [
@@ -43,9 +43,14 @@ def cdiag_from_b(kappa, b_int):
 
 
 class Problem:
-    """Leaf maps of a whole grid: R (N_l, n_b, n_b) and H (N_l, n_b, n_i)."""
+    """Leaf maps of a whole grid: R (N_l, n_b, n_b) and H (N_l, n_b, n_i).
 
-    def __init__(self, grid, kappa, eta, b_int, leaves=None, homogenized=False):
+    With homogenized=True the maps are R~, H~ (C replaced by lambda^tau,
+    Sec. 4.1), lambda^tau optionally binned over the whole grid
+    (`binned_lambdas`, lambda_bin = delta).
+    """
+
+    def __init__(self, grid, kappa, eta, b_int, leaves=None, homogenized=False, lambda_bin=0.0):
         self.grid = grid
         self.kappa = kappa
         self.eta = eta
@@ -55,18 +60,23 @@ class Problem:
         self.leaves = list(leaves)
         self.R = {}
         self.H = {}
+        self.lam = None
+        if homogenized:
+            lams = [homogenized_lambda(cdiag_from_b(kappa, self.b_int[i])) for i in range(grid.nleaves)]
+            self.lam = binned_lambdas(lams, lambda_bin)
         for leaf in self.leaves:
-            c = cdiag_from_b(kappa, self.b_int[leaf])
             if homogenized:
-                c = np.full(L.ni, homogenized_lambda(c), dtype=np.complex128)
+                c = np.full(L.ni, self.lam[leaf], dtype=np.complex128)
+            else:
+                c = cdiag_from_b(kappa, self.b_int[leaf])
             self.R[leaf], self.H[leaf] = leaf_iti(grid.p, grid.h, eta, c)
 
     def R_array(self):
         return np.stack([self.R[i] for i in range(self.grid.nleaves)])
 
 
-def build_problem(grid, kappa, eta, b_int, leaves=None, homogenized=False):
-    return Problem(grid, kappa, eta, b_int, leaves, homogenized)
+def build_problem(grid, kappa, eta, b_int, leaves=None, homogenized=False, lambda_bin=0.0):
+    return Problem(grid, kappa, eta, b_int, leaves, homogenized, lambda_bin)
 
 
 def _faces(grid, v):
