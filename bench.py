@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--L", type=int, default=16, help="leaves per axis (16 = the benchmark workload)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / no-preconditioner comparison runs")
     ap.add_argument("--cpu-sample-L", type=int, default=4)
-    ap.add_argument("--serving-requests", type=int, default=16,
+    ap.add_argument("--serving-requests", type=int, default=8,
                     help="requests of the scaled serving stream timed after the solves (0 = skip)")
     return ap.parse_args()
 
@@ -358,19 +358,20 @@ def run_gpu(args, dist):
 
 def run_serving(args, dist):
     """A bounded, scaled sample of the serving stream: Poisson arrivals at 20/s, grids of
-    4^3-8^3 leaves, p in {8, 10}, kappa in [20, 60], 3-8 bumps, 1-16 sources; mixed form,
+    4^3-6^3 leaves, p in {8, 10}, kappa in [20, 60], 3-8 bumps, 1-16 sources; mixed form,
     tol 1e-6, admission by an HBM budget of 64 GiB, up to 4 requests in flight.
-    Latency = arrival to result on the host, including setup."""
+    Latency = arrival to result on the host, including each request's setup (its own
+    medium, so its own leaf maps)."""
     from paper_2112_02211_gb300.serving import HPSBackend, Request, Server, latency_stats
 
-    ws = W.serving_stream(n=args.serving_requests, rate=20.0, seed=7, L_range=(4, 8), p_choices=(8, 10),
+    ws = W.serving_stream(n=args.serving_requests, rate=20.0, seed=7, L_range=(4, 6), p_choices=(8, 10),
                           kappa_range=(20.0, 60.0), max_sources=16)
     reqs = [Request(i, w, w.meta["arrival"]) for i, w in enumerate(ws)]
     srv = Server(HPSBackend(form="mixed", device=dist.local), hbm_budget=64 << 30, max_active=4)
     res = srv.run(reqs)
     st = latency_stats(res)
     st.update({"requests": len(reqs), "peak_active": srv.peak_active, "peak_budget_bytes": srv.peak_bytes,
-               "stream": "serving recipe scaled to 4^3-8^3 leaves, p in {8,10}, kappa in [20,60]; "
+               "stream": "serving recipe scaled to 4^3-6^3 leaves, p in {8,10}, kappa in [20,60]; "
                          "latency includes per-request setup"})
     return st
 

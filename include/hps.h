@@ -93,6 +93,11 @@ typedef struct {
                          scale per row and use them in hps_gmres_solve (default 1) */
   int tc_apply;       /* complex-FP32 apply of 64, 128, ... right-hand sides on the tensor cores
                          (three TF32 products, FP32 accumulation; default 1) */
+  int lean;           /* memory-lean mixed form (forms must be HPS_FORM_MIXED): the exact leaf
+                         maps R, H are eliminated in FP64 but kept only in FP32, the cluster
+                         inverses only in FP16, and the restart residual uses the FP32 maps with
+                         FP64 vectors (about 1e-7 relative per apply, for tolerances >= 1e-5).
+                         HPS_C128 applies are then unavailable.  Default 0. */
 } hps_options;
 
 typedef struct {

@@ -66,7 +66,8 @@ class Solver:
     """One medium on one grid: leaf ItI maps, preconditioner and Krylov workspace on the GPU."""
 
     def __init__(self, nx, ny, nz, p, kappa, eta=None, b=None, forms=("fp64", "mixed"), restart=50,
-                 cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0, precond_fp16=True, tc_apply=True):
+                 cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0, precond_fp16=True, tc_apply=True,
+                 lean=False):
         self.lib = N.load()
         self.nx, self.ny, self.nz, self.p, self.q = nx, ny, nz, p, p - 2
         self.nl = nx * ny * nz
@@ -88,6 +89,7 @@ class Solver:
         opt.device = device
         opt.precond_fp16 = 1 if precond_fp16 else 0
         opt.tc_apply = 1 if tc_apply else 0
+        opt.lean = 1 if lean else 0
         bb = None
         if b is not None:
             bb = np.ascontiguousarray(np.asarray(b, dtype=np.complex128).reshape(-1))

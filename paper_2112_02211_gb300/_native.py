@@ -37,7 +37,8 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("forms", ctypes.c_int), ("restart", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("max_rhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
-                ("device", ctypes.c_int), ("precond_fp16", ctypes.c_int), ("tc_apply", ctypes.c_int)]
+                ("device", ctypes.c_int), ("precond_fp16", ctypes.c_int), ("tc_apply", ctypes.c_int),
+                ("lean", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -6,7 +6,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -19,6 +22,31 @@ thread_local std::string g_err;
 }
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> limits;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(kernel, dev);
+  auto it = limits.find(key);
+  if (it == limits.end()) {
+    int mx = 0;
+    e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    // the opt-in maximum covers static plus dynamic shared memory
+    const int dyn = mx - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    it = limits.emplace(key, dyn).first;
+  }
+  return bytes <= (size_t)it->second ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 cudaError_t launch_cdiag(const double2* b, double kappa, long long count, double2* c, cudaStream_t st);
 
@@ -82,7 +110,7 @@ void free_handle(hps_handle* h) {
   cudaSetDevice(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
   krylov_free(h);
-  void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->lambda, h->Kc64, h->Kc32, h->B64, h->B32, h->pc_scratch,
+  void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->H32, h->lambda, h->Kc64, h->Kc32, h->B64, h->B32, h->pc_scratch,
                   h->Kc16, h->Kc16s, h->B16, h->B16s, h->tc_error, h->cdiag,
                   h->dct.slot_lf, h->dct.slot_cluster, h->dct.cl_slot_begin, h->dct.cl_kc_off, h->dct.lf_slot,
                   h->dct.int_mask, h->dct.b_off};
@@ -130,6 +158,10 @@ int check_options(const hps_options& o) {
     set_error("bad options (max_rhs, maxit or forms)");
     return HPS_EINVAL;
   }
+  if (o.lean && o.forms != HPS_FORM_MIXED) {
+    set_error("lean mode keeps FP32 maps only: forms must be HPS_FORM_MIXED");
+    return HPS_EINVAL;
+  }
   return HPS_OK;
 }
 
@@ -157,6 +189,7 @@ void hps_default_options(hps_options* o) {
   o->device = 0;
   o->precond_fp16 = 1;
   o->tc_apply = 1;
+  o->lean = 0;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -222,15 +255,18 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
     int r;
     if ((r = dalloc(h, (void**)&h->tables, h->tl.total * sizeof(double)))) return r;
     const size_t rel = (size_t)h->nl * h->nb * h->ldR;
-    if ((r = dalloc(h, (void**)&h->R64, rel * sizeof(double2)))) return r;
+    const size_t hel = (size_t)h->nl * h->nb * h->ldH;
+    if (!o.lean && (r = dalloc(h, (void**)&h->R64, rel * sizeof(double2)))) return r;
     if (want32 && (r = dalloc(h, (void**)&h->R32, rel * sizeof(float2)))) return r;
-    if ((r = dalloc(h, (void**)&h->H64, (size_t)h->nl * h->nb * h->ldH * sizeof(double2)))) return r;
+    if (!o.lean && (r = dalloc(h, (void**)&h->H64, hel * sizeof(double2)))) return r;
+    if (o.lean && (r = dalloc(h, (void**)&h->H32, hel * sizeof(float2)))) return r;
     if ((r = dalloc(h, (void**)&h->lambda, (size_t)h->nl * sizeof(double2)))) return r;
     if ((r = dalloc(h, (void**)&h->tc_error, sizeof(int)))) return r;
     HPS_CUDA_TRY(cudaMemsetAsync(h->tc_error, 0, sizeof(int), st));
-    HPS_CUDA_TRY(cudaMemsetAsync(h->R64, 0, rel * sizeof(double2), st));
+    if (h->R64) HPS_CUDA_TRY(cudaMemsetAsync(h->R64, 0, rel * sizeof(double2), st));
     if (h->R32) HPS_CUDA_TRY(cudaMemsetAsync(h->R32, 0, rel * sizeof(float2), st));
-    HPS_CUDA_TRY(cudaMemsetAsync(h->H64, 0, (size_t)h->nl * h->nb * h->ldH * sizeof(double2), st));
+    if (h->H64) HPS_CUDA_TRY(cudaMemsetAsync(h->H64, 0, hel * sizeof(double2), st));
+    if (h->H32) HPS_CUDA_TRY(cudaMemsetAsync(h->H32, 0, hel * sizeof(float2), st));
     HPS_CUDA_TRY(cudaMalloc(&db, (size_t)h->nint * sizeof(double2)));
     if ((r = dalloc(h, (void**)&h->cdiag, (size_t)h->nint * sizeof(double2)))) return r;
     dc = h->cdiag;
@@ -251,16 +287,16 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
         HPS_CUDA_TRY(cudaMemsetAsync(h->Kc64, 0, std::max<long long>(1, ct.kc_elems) * sizeof(double2), st));
         HPS_CUDA_TRY(cudaMemsetAsync(h->B64, 0, std::max<long long>(1, ct.b_elems) * sizeof(double2), st));
       }
+      const bool fp16 = want32 && (o.precond_fp16 || o.lean);
       if (want32) {
-        if ((r = dalloc(h, (void**)&h->Kc32, std::max<long long>(1, ct.kc_elems) * sizeof(float2)))) return r;
+        if (!o.lean &&
+            (r = dalloc(h, (void**)&h->Kc32, std::max<long long>(1, ct.kc_elems) * sizeof(float2))))
+          return r;
         if ((r = dalloc(h, (void**)&h->B32, std::max<long long>(1, ct.b_elems) * sizeof(float2)))) return r;
-        HPS_CUDA_TRY(cudaMemsetAsync(h->Kc32, 0, std::max<long long>(1, ct.kc_elems) * sizeof(float2), st));
+        if (h->Kc32) HPS_CUDA_TRY(cudaMemsetAsync(h->Kc32, 0, std::max<long long>(1, ct.kc_elems) * sizeof(float2), st));
         HPS_CUDA_TRY(cudaMemsetAsync(h->B32, 0, std::max<long long>(1, ct.b_elems) * sizeof(float2), st));
       }
-      const size_t ts = std::max<size_t>(1, (size_t)ct.nslots * h->q * h->q) * o.max_rhs * sizeof(double2);
-      if ((r = dalloc(h, &h->pc_scratch, ts))) return r;
-      if ((r = build_preconditioner(h, dc, st))) return r;
-      if (want32 && o.precond_fp16) {
+      if (fp16) {
         const int q2 = h->q * h->q;
         const size_t ke = std::max<long long>(1, ct.kc_elems), be = std::max<long long>(1, ct.b_elems);
         if ((r = dalloc(h, (void**)&h->Kc16, ke * sizeof(__half2)))) return r;
@@ -269,8 +305,11 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
         if ((r = dalloc(h, (void**)&h->B16s, (size_t)h->nl * 6 * q2 * sizeof(float)))) return r;
         HPS_CUDA_TRY(cudaMemsetAsync(h->Kc16, 0, ke * sizeof(__half2), st));
         HPS_CUDA_TRY(cudaMemsetAsync(h->B16, 0, be * sizeof(__half2), st));
-        if ((r = build_precond_fp16(h, st))) return r;
       }
+      const size_t ts = std::max<size_t>(1, (size_t)ct.nslots * h->q * h->q) * o.max_rhs * sizeof(double2);
+      if ((r = dalloc(h, &h->pc_scratch, ts))) return r;
+      if ((r = build_preconditioner(h, dc, st))) return r;
+      if (fp16 && (r = build_precond_fp16(h, st))) return r;
     }
     HPS_CUDA_TRY(cudaStreamSynchronize(st));
     return HPS_OK;
@@ -300,8 +339,9 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
   const bool want64 = (o.forms & HPS_FORM_FP64) != 0, want32 = (o.forms & HPS_FORM_MIXED) != 0;
   const size_t c16 = sizeof(double2), c8 = sizeof(float2);
   const size_t rel = (size_t)h.nl * h.nb * h.ldR;
-  size_t bytes = h.tl.total * sizeof(double) + rel * c16 + (want32 ? rel * c8 : 0) +
-                 (size_t)h.nl * h.nb * h.ldH * c16 + (size_t)h.nl * c16;
+  const size_t hel = (size_t)h.nl * h.nb * h.ldH;
+  size_t bytes = h.tl.total * sizeof(double) + (o.lean ? 0 : rel * c16) + (want32 ? rel * c8 : 0) +
+                 hel * (o.lean ? c8 : c16) + (size_t)h.nl * c16;
   const int q2 = h.q * h.q;
   size_t nslots = 0;
   if (o.cluster == 2) {
@@ -312,8 +352,8 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
              ct.cl_kc_off.size() * sizeof(long long) + ct.lf_slot.size() * sizeof(int) + ct.int_mask.size() +
              ct.b_off.size() * sizeof(long long);
     if (want64) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c16;
-    if (want32) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c8;
-    if (want32 && o.precond_fp16)
+    if (want32) bytes += (size_t)((o.lean ? 0 : ct.kc_elems) + ct.b_elems) * c8;
+    if (want32 && (o.precond_fp16 || o.lean))
       bytes += (size_t)(ct.kc_elems + ct.b_elems) * sizeof(__half2) + nslots * q2 * sizeof(float) +
                (size_t)h.nl * 6 * q2 * sizeof(float);
     bytes += std::max<size_t>(1, nslots * q2) * o.max_rhs * c16;
@@ -322,7 +362,7 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
   // Krylov workspace of one solve (host inputs staged on the device)
   const int M1 = o.restart + 1;
   const size_t vb = (size_t)nrhs * h.nf * c16;
-  const long long nblk = (h.nf + 511) / 512;
+  const long long nblk = (h.nf + 1023) / 1024;
   bytes += vb * (M1 + 5) + std::max<size_t>(1, nslots * q2) * nrhs * c16 + (size_t)nrhs * nblk * M1 * c16 +
            (size_t)o.max_rhs * (h.nint + h.nf) * c16 + (size_t)nrhs * (3 * M1 + 4 * o.restart + 8) * c16 +
            (size_t)nrhs * std::max<long long>(256, nblk) * sizeof(double);
@@ -341,6 +381,10 @@ int hps_apply(hps_handle* h, int dtype, const void* f, void* y, int nrhs, void* 
   HPS_CUDA_TRY(cudaSetDevice(h->dev));
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == HPS_C128) {
+    if (!h->R64) {
+      set_error("hps_apply: complex-double maps are not kept in lean mode");
+      return HPS_EINVAL;
+    }
     HPS_CUDA_TRY(launch_apply(h, false, VType::C128, f, VType::C128, y, nullptr, nrhs, false, st));
   } else if (dtype == HPS_C64) {
     if (!h->R32) {
@@ -388,11 +432,12 @@ int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void
     }
     HPS_CUDA_TRY(launch_precond(h, true, VType::C64, r, VType::C64, z, h->pc_scratch, nrhs, st, true));
   } else {
-    if (!h->Kc32) {
+    if (!h->Kc32 && !h->Kc16) {
       set_error("hps_precond: FP32 preconditioner was not built (HPS_FORM_MIXED)");
       return HPS_EINVAL;
     }
-    HPS_CUDA_TRY(launch_precond(h, true, VType::C64, r, VType::C64, z, h->pc_scratch, nrhs, st));
+    // lean mode keeps the cluster inverses in FP16 only
+    HPS_CUDA_TRY(launch_precond(h, true, VType::C64, r, VType::C64, z, h->pc_scratch, nrhs, st, !h->Kc32));
   }
   return HPS_OK;
 }
@@ -425,6 +470,10 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
   }
   if (form == HPS_FORM_MIXED && (!h->R32 || (h->has_precond && !no_pc && !h->Kc32))) {
     set_error("hps_gmres_solve: mixed-form operators were not built");
+    return HPS_EINVAL;
+  }
+  if (form == HPS_FORM_FP64 && !h->R64) {
+    set_error("hps_gmres_solve: the FP64 form needs the complex-double maps (not kept in lean mode)");
     return HPS_EINVAL;
   }
   if (form == HPS_FORM_FP64 && h->has_precond && !no_pc && !h->Kc64) {
@@ -514,9 +563,11 @@ long long hps_export(hps_handle* h, int what, int index, double* host_out) {
   switch (what) {
     case HPS_EXPORT_R:
       if (index < 0 || index >= h->nl) break;
+      if (!h->R64) return copy2d(h->R32 + (size_t)index * h->nb * h->ldR, sizeof(float2), h->nb, h->nb, h->ldR, true);
       return copy2d(h->R64 + (size_t)index * h->nb * h->ldR, sizeof(double2), h->nb, h->nb, h->ldR, false);
     case HPS_EXPORT_H:
       if (index < 0 || index >= h->nl) break;
+      if (!h->H64) return copy2d(h->H32 + (size_t)index * h->nb * h->ldH, sizeof(float2), h->nb, h->ni, h->ldH, true);
       return copy2d(h->H64 + (size_t)index * h->nb * h->ldH, sizeof(double2), h->nb, h->ni, h->ldH, false);
     case HPS_EXPORT_LAMBDA:
       if (index < 0 || index >= h->nl || !h->has_precond) break;

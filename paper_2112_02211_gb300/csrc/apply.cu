@@ -155,11 +155,12 @@ struct ApplyP {
   }
 };
 
+template <class TM_>
 struct RhsP {
-  using TM = double2;
-  using Acc = double2;
+  using TM = TM_;
+  using Acc = typename MT<TM>::Acc;
   struct Args {
-    const double2* H;
+    const TM* H;
     int ldH, ni, nb, q2;
     GridDims g;
     const double2* s;
@@ -187,12 +188,13 @@ struct RhsP {
     return true;
   }
   __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
-    return A.s[rhs * A.nint + it.xoff + c];
+    return cvt<Acc>(A.s[rhs * A.nint + it.xoff + c]);
   }
   __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
     for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
       const int rhs = idx / A.q2, j = idx % A.q2;
-      A.out[rhs * A.nf + it.ooff + j] = make_double2(-outs[idx].x, -outs[idx].y);
+      const double2 v = cvt<double2>(outs[idx]);
+      A.out[rhs * A.nf + it.ooff + j] = make_double2(-v.x, -v.y);
     }
   }
   __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
@@ -401,7 +403,7 @@ cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm,
   using Acc = typename P::Acc;
   const size_t smem = ((size_t)NR * xcap + (size_t)NR * rowcap) * sizeof(Acc);
   auto kern = seg_gemv_kernel<P, NR, RPW>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
@@ -536,18 +538,19 @@ cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const
       return apply_t(h, h->R64, (const double2*)f, (double2*)y, bvec, nrhs, st);
     return cudaErrorInvalidValue;
   }
+  // the residual form b - (I + Pi R) f only exists for complex-double vectors
+  if (bvec && !(tin == VType::C128 && tout == VType::C128)) return cudaErrorInvalidValue;
   const bool tc = h->opt.tc_apply && h->tc_error && nrhs >= 64 && nrhs % 64 == 0 && !bvec;
   if (tc && tin == VType::C64 && tout == VType::C64)
     return launch_apply_tc(h, (const float2*)f, y, false, nrhs, h->tc_error, st);
   if (tc && tin == VType::C64 && tout == VType::DF)
     return launch_apply_tc(h, (const float2*)f, y, true, nrhs, h->tc_error, st);
   if (tin == VType::C64 && tout == VType::C64)
-    return apply_t(h, h->R32, (const float2*)f, (float2*)y, bvec, nrhs, st);
-  if (bvec) return cudaErrorInvalidValue;
+    return apply_t(h, h->R32, (const float2*)f, (float2*)y, nullptr, nrhs, st);
   if (tin == VType::C64 && tout == VType::C128)
     return apply_t(h, h->R32, (const float2*)f, (double2*)y, nullptr, nrhs, st);
   if (tin == VType::C128 && tout == VType::C128)
-    return apply_t(h, h->R32, (const double2*)f, (double2*)y, nullptr, nrhs, st);
+    return apply_t(h, h->R32, (const double2*)f, (double2*)y, bvec, nrhs, st);
   if (tin == VType::C64 && tout == VType::DF)
     return apply_t(h, h->R32, (const float2*)f, (float4*)y, nullptr, nrhs, st);
   if (tin == VType::DF && tout == VType::DF)
@@ -563,10 +566,12 @@ cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType 
   return e;
 }
 
-cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
-                       cudaStream_t st) {
-  typename RhsP::Args A;
-  A.H = h->H64;
+template <class TM>
+cudaError_t rhs_t(const hps_handle* h, const TM* H, const double2* s, const double2* t, double2* b, int nrhs,
+                  cudaStream_t st) {
+  using P = RhsP<TM>;
+  typename P::Args A;
+  A.H = H;
   A.ldH = h->ldH;
   A.ni = h->ni;
   A.nb = h->nb;
@@ -579,11 +584,17 @@ cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, 
   A.nint = h->nint;
   A.nrhs = nrhs;
   A.nitems = (long long)h->nl * 6;
-  return launch_groups<RhsP>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename RhsP::Args& B, int r0) {
+  return launch_groups<P>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename P::Args& B, int r0) {
     if (B.s) B.s += (long long)r0 * h->nint;
     if (B.t) B.t += (long long)r0 * h->nf;
     B.out += (long long)r0 * h->nf;
   });
+}
+
+cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
+                       cudaStream_t st) {
+  if (h->H64) return rhs_t(h, h->H64, s, t, b, nrhs, st);
+  return rhs_t(h, h->H32, s, t, b, nrhs, st);
 }
 
 cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, const void* r, VType tout, void* z,

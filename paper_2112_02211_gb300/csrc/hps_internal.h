@@ -29,6 +29,12 @@ void set_error(const std::string& msg);
 
 inline long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+// Lets `kernel` use up to `bytes` of dynamic shared memory.  The limit is a
+// per-function attribute shared by every host thread, so it is raised once per
+// (kernel, device) to the device's opt-in maximum and never lowered: concurrent
+// callers needing different amounts cannot set it below each other's launch.
+cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes);
+
 // Offsets (in doubles) of the 1D tables in Handle::tables.
 struct TableLayout {
   int p, q;
@@ -180,6 +186,7 @@ struct hps_handle {
   double2* R64 = nullptr;  // nl x nb x ldR
   float2* R32 = nullptr;   // nl x nb x ldR
   double2* H64 = nullptr;  // nl x nb x ldH
+  float2* H32 = nullptr;   // nl x nb x ldH (lean mode instead of H64)
   double2* lambda = nullptr;  // nl
   double2* cdiag = nullptr;   // nl x ni: C = kappa^2 (1 - b) at interior nodes (kept for recovery)
 

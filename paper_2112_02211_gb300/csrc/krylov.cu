@@ -14,7 +14,7 @@
 // correction equation with the FP32 operator and the FP64 residual drives the
 // next cycle (iterative refinement with a GMRES inner solver).
 //
-// Dot products are formed as fixed-order block partials (512 entries per
+// Dot products are formed as fixed-order block partials (1024 entries per
 // block, warp shuffles, then a sequential sum over blocks), so results are
 // bitwise reproducible run to run.
 #include <algorithm>
@@ -30,9 +30,9 @@ namespace hps {
 namespace {
 
 constexpr int kT = 256;      // threads per block
-constexpr int kE = 2;        // vector entries per thread (512 per block: enough blocks to fill the GPU)
+constexpr int kE = 4;        // vector entries per thread (1024 per block)
 constexpr int kChunk = kT * kE;
-constexpr int kG = 8;        // vectors per register group
+constexpr int kG = 4;        // vectors per register group
 
 __device__ __forceinline__ void block_reduce_store(double2 (&acc)[kG], int ng, double2* out) {
   __shared__ double2 red[kT / 32][kG];
@@ -186,31 +186,64 @@ struct DfArgs {
   const int* active;
 };
 
-// Warp-level double-float sums, then one FP64 value per warp, summed over the
-// warps in a fixed order.
-__device__ __forceinline__ void block_reduce_store_df(dfc (&acc)[kG], int ng, double2* out) {
-  __shared__ double2 red[kT / 32][kG];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Compensated accumulation in the spirit of Ogita, Rump and Oishi's Dot2:
+// acc = (s, c) with s the running FP32 sum and c the collected rounding errors.
+// A term a*b of two double-float numbers adds its exact hi*hi product (FMA
+// TwoProduct), the cross terms a.h*b.l + a.l*b.h in FP32, and the TwoSum error.
+struct acc2 {
+  float s, c;
+};
+__device__ __forceinline__ void acc2_madd(acc2& a, dfr x, dfr y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  const dfr t = df_two_sum(a.s, p);
+  a.s = t.h;
+  a.c = __fadd_rn(a.c, __fadd_rn(t.l, e));
+}
+__device__ __forceinline__ void acc2_msub(acc2& a, dfr x, dfr y) { acc2_madd(a, {-x.h, -x.l}, y); }
+__device__ __forceinline__ dfr acc2_value(acc2 a) { return df_two_sum(a.s, a.c); }
+
+// conj(v) * w accumulated into (re, im)
+__device__ __forceinline__ void conjdot_acc(acc2& re, acc2& im, dfc v, dfc w) {
+  acc2_madd(re, v.re, w.re);
+  acc2_madd(re, v.im, w.im);
+  acc2_madd(im, v.re, w.im);
+  acc2_msub(im, v.im, w.re);
+}
+
+// Block sums of kG double-float complex partials per thread: the partials go
+// through shared memory transposed, so each thread finishes with one warp
+// reduction for the whole group.  Result per vector as complex double.
+__device__ __forceinline__ void block_reduce_store_df(dfc (&part)[kG], int ng, double2* out) {
+  __shared__ dfc red[kG][kT];
+  __shared__ dfc red2[kG][kT / 32 / kG > 0 ? kT / 32 / kG : 1];
+  static_assert(kT % (32 * kG) == 0, "block must split into kG groups of whole warps");
+  constexpr int kPer = kT / kG;  // threads per vector in the transposed sum
+  const int tid = threadIdx.x, lane = tid & 31;
 #pragma unroll
-  for (int g = 0; g < kG; ++g) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      dfc other;
-      other.re.h = __shfl_xor_sync(0xffffffffu, acc[g].re.h, o);
-      other.re.l = __shfl_xor_sync(0xffffffffu, acc[g].re.l, o);
-      other.im.h = __shfl_xor_sync(0xffffffffu, acc[g].im.h, o);
-      other.im.l = __shfl_xor_sync(0xffffffffu, acc[g].im.l, o);
-      acc[g] = dfc_add(acc[g], other);
-    }
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int g = 0; g < kG; ++g) red[warp][g] = dfc_to_double2(acc[g]);
+  for (int g = 0; g < kG; ++g) red[g][tid] = part[g];
   __syncthreads();
-  if (threadIdx.x < ng) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int w = 0; w < kT / 32; ++w) s = cadd(s, red[w][threadIdx.x]);
-    out[threadIdx.x] = s;
+  const int g = tid / kPer, k = tid % kPer;
+  dfc a = dfc_zero();
+#pragma unroll
+  for (int m = 0; m < kT / kPer; ++m) a = dfc_add(a, red[g][k + kPer * m]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dfc other;
+    other.re.h = __shfl_xor_sync(0xffffffffu, a.re.h, o);
+    other.re.l = __shfl_xor_sync(0xffffffffu, a.re.l, o);
+    other.im.h = __shfl_xor_sync(0xffffffffu, a.im.h, o);
+    other.im.l = __shfl_xor_sync(0xffffffffu, a.im.l, o);
+    a = dfc_add(a, other);
+  }
+  if (lane == 0) red2[g][k / 32] = a;
+  __syncthreads();
+  if (k == 0 && g < ng) {
+    dfc t = red2[g][0];
+    for (int w = 1; w < kPer / 32; ++w) t = dfc_add(t, red2[g][w]);
+    out[g] = dfc_to_double2(t);
   }
   __syncthreads();
 }
@@ -218,21 +251,24 @@ __device__ __forceinline__ void block_reduce_store_df(dfc (&acc)[kG], int ng, do
 __device__ __forceinline__ void df_dots(const DfArgs& a, int rhs, long long base, const dfc (&wv)[kE], double2* out) {
   for (int g0 = 0; g0 < a.nvec; g0 += kG) {
     const int ng = min(kG, a.nvec - g0);
-    dfc acc[kG];
-#pragma unroll
-    for (int g = 0; g < kG; ++g) acc[g] = dfc_zero();
+    dfc part[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
+      acc2 re{0.f, 0.f}, im{0.f, 0.f};
       if (g < ng) {
         const float4* v = a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf;
+        float4 vv[kE];
 #pragma unroll
         for (int e = 0; e < kE; ++e) {
           const long long i = base + (long long)e * kT;
-          if (i < a.nf) acc[g] = dfc_add(acc[g], dfc_conjmul(dfc_load(v[i]), wv[e]));
+          vv[e] = (i < a.nf) ? v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int e = 0; e < kE; ++e) conjdot_acc(re, im, dfc_load(vv[e]), wv[e]);
       }
+      part[g] = {acc2_value(re), acc2_value(im)};
     }
-    block_reduce_store_df(acc, ng, out + g0);
+    block_reduce_store_df(part, ng, out + g0);
   }
 }
 
@@ -259,24 +295,38 @@ __global__ void __launch_bounds__(kT) axpy_df_kernel(DfArgs a, int mode) {
   __syncthreads();
   const long long base = (long long)blk * kChunk + threadIdx.x;
   float4* w = a.w + rhs * a.nf;
-  dfc wv[kE];
+  acc2 wr[kE], wi[kE];
 #pragma unroll
   for (int e = 0; e < kE; ++e) {
     const long long i = base + (long long)e * kT;
-    wv[e] = (i < a.nf) ? dfc_load(w[i]) : dfc_zero();
+    const dfc x = (i < a.nf) ? dfc_load(w[i]) : dfc_zero();
+    wr[e] = {x.re.h, x.re.l};
+    wi[e] = {x.im.h, x.im.l};
   }
-#pragma unroll 4
+#pragma unroll 2
   for (int j = 0; j < a.nvec; ++j) {
     const float4* v = a.V + ((long long)j * a.nrhs + rhs) * a.nf;
     const dfc c = cf[j];
+    float4 vv[kE];
 #pragma unroll
     for (int e = 0; e < kE; ++e) {
       const long long i = base + (long long)e * kT;
-      if (i < a.nf) wv[e] = dfc_sub(wv[e], dfc_mul(c, dfc_load(v[i])));
+      vv[e] = (i < a.nf) ? v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      const dfc x = dfc_load(vv[e]);
+      // w -= c x:  re -= c.re x.re - c.im x.im,  im -= c.re x.im + c.im x.re
+      acc2_msub(wr[e], c.re, x.re);
+      acc2_madd(wr[e], c.im, x.im);
+      acc2_msub(wi[e], c.re, x.im);
+      acc2_msub(wi[e], c.im, x.re);
     }
   }
+  dfc wv[kE];
 #pragma unroll
   for (int e = 0; e < kE; ++e) {
+    wv[e] = {acc2_value(wr[e]), acc2_value(wi[e])};
     const long long i = base + (long long)e * kT;
     if (i < a.nf) w[i] = dfc_store(wv[e]);
   }
@@ -284,13 +334,17 @@ __global__ void __launch_bounds__(kT) axpy_df_kernel(DfArgs a, int mode) {
   if (mode == 1) {
     df_dots(a, rhs, base, wv, out);
   } else if (mode == 2) {
-    dfc acc[kG];
+    dfc part[kG];
 #pragma unroll
-    for (int g = 0; g < kG; ++g) acc[g] = dfc_zero();
+    for (int g = 0; g < kG; ++g) part[g] = dfc_zero();
+    acc2 n2{0.f, 0.f};
 #pragma unroll
-    for (int e = 0; e < kE; ++e)
-      acc[0].re = df_add(acc[0].re, df_add(df_mul(wv[e].re, wv[e].re), df_mul(wv[e].im, wv[e].im)));
-    block_reduce_store_df(acc, 1, out);
+    for (int e = 0; e < kE; ++e) {
+      acc2_madd(n2, wv[e].re, wv[e].re);
+      acc2_madd(n2, wv[e].im, wv[e].im);
+    }
+    part[0].re = acc2_value(n2);
+    block_reduce_store_df(part, 1, out);
   }
 }
 
@@ -775,7 +829,9 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     h->prof.end(HPS_PHASE_UPDATE, ev_up, st);
     h->prof.launches += 3;
     // true residual with the FP64 maps
-    HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_RESIDUAL, false, VType::C128, x, VType::C128, k.r, b, nrhs, true, st));
+    // FP64 maps, or in lean mode the FP32 maps against FP64 vectors
+    HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_RESIDUAL, h->R64 == nullptr, VType::C128, x, VType::C128, k.r, b, nrhs,
+                             true, st));
     if ((rc = vec_norms(h, k.r, nrhs, rnorm, st))) return rc;
     if (h->tc_error) {
       int terr = 0;

@@ -610,6 +610,23 @@ __global__ void quantize_kc_kernel(const float2* K32, __half2* K16, float* kscal
   }
 }
 
+// K_c rows of one batch straight from the elimination workspace (columns
+// [nint, 2 nint) of each cluster's [I + D | I]) into FP16 with row scales.
+__global__ void quantize_kc_ws_kernel(const float2* W, long long wstride, int ldw, int cl0, int nbatch,
+                                      const int* cl_slot_begin, const long long* kc_off, int q2, __half2* K16,
+                                      float* kscale) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  const int c = cl0 + b;
+  const int s0 = cl_slot_begin[c];
+  const int nint = (cl_slot_begin[c + 1] - s0) * q2;
+  const int ldk = (int)rup4(nint);
+  for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nint; r += gridDim.x * (blockDim.x >> 5))
+    quantize_row(W + (long long)b * wstride + (long long)r * ldw + nint, K16 + kc_off[c] + (long long)r * ldk, nint,
+                 kscale + (long long)s0 * q2 + r, lane);
+}
+
 // rows of every B^leaf; row index (leaf*6 + face)*q^2 + j for internal faces
 __global__ void quantize_b_kernel(const float2* B32, __half2* B16, float* bscale, const uint8_t* int_mask,
                                   const long long* b_off, int q2, long long nrows) {
@@ -635,7 +652,7 @@ int build_precond_fp16(hps_handle* h, cudaStream_t st) {
   const int q2 = h->q * h->q;
   const long long krows = (long long)h->ct.nslots * q2;
   const long long brows = (long long)h->nl * 6 * q2;
-  if (krows > 0) {
+  if (krows > 0 && h->Kc32) {  // lean mode quantized K_c during the build
     quantize_kc_kernel<<<h->nsm * 8, 256, 0, st>>>(h->Kc32, h->Kc16, h->Kc16s, h->dct.slot_cluster,
                                                     h->dct.cl_slot_begin, h->dct.cl_kc_off, q2, krows);
     HPS_CUDA_TRY(cudaGetLastError());
@@ -671,8 +688,7 @@ template <class T>
 cudaError_t run_gj(T* W, long long wstride, int ld, int n, int ncols, int gj0, int nbatch, int* status,
                    cudaStream_t st) {
   const size_t smem = (size_t)ncols * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(gj_kernel<T, kGjThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)gj_kernel<T, kGjThreads>, smem);
   if (e != cudaSuccess) return e;
   gj_kernel<T, kGjThreads><<<nbatch, kGjThreads, smem, st>>>(W, wstride, ld, n, ncols, gj0, nbatch, status);
   return cudaGetLastError();
@@ -683,7 +699,7 @@ cudaError_t run_seg_kron(T* M, long long mstride, int ld, int nrows, int ncols, 
                          const double* tables, const TableLayout& tl, int trans, int mode, int nsm, cudaStream_t st) {
   const int q2 = tl.q * tl.q;
   const size_t smem = 8 * 2 * q2 * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(seg_kron_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)seg_kron_kernel<T>, smem);
   if (e != cudaSuccess) return e;
   seg_kron_kernel<T><<<nsm * 8, 256, smem, st>>>(M, mstride, ld, nrows, ncols, nbatch, tables, tl, trans, mode);
   return cudaGetLastError();
@@ -797,9 +813,16 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
   exact_maps_workspace(h, workspace_budget(h), &nbatch);
   double2* W = nullptr;
   int* d_status = nullptr;
+  double2 *Rtmp = nullptr, *Htmp = nullptr;  // lean mode: FP64 maps of one batch before rounding
   HPS_CUDA_TRY(cudaMalloc(&W, per * nbatch));
   HPS_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
   HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  if (!h->R64) {
+    HPS_CUDA_TRY(cudaMalloc(&Rtmp, (size_t)nbatch * nb * h->ldR * sizeof(double2)));
+    HPS_CUDA_TRY(cudaMalloc(&Htmp, (size_t)nbatch * nb * h->ldH * sizeof(double2)));
+    HPS_CUDA_TRY(cudaMemsetAsync(Rtmp, 0, (size_t)nbatch * nb * h->ldR * sizeof(double2), st));
+    HPS_CUDA_TRY(cudaMemsetAsync(Htmp, 0, (size_t)nbatch * nb * h->ldH * sizeof(double2), st));
+  }
   int rc = HPS_OK;
   for (int l0 = 0; l0 < h->nl && rc == HPS_OK; l0 += nbatch) {
     const int nbt = std::min(nbatch, h->nl - l0);
@@ -810,8 +833,8 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
                                                   cdiag, nullptr, 2);
       HPS_CUDA_TRY(cudaGetLastError());
       HPS_CUDA_TRY(run_gj(W, wstride, ld, n, ncols, ni, nbt, d_status, st));
-      double2* Rb = h->R64 + (long long)l0 * nb * h->ldR;
-      double2* Hb = h->H64 + (long long)l0 * nb * h->ldH;
+      double2* Rb = h->R64 ? h->R64 + (long long)l0 * nb * h->ldR : Rtmp;
+      double2* Hb = h->H64 ? h->H64 + (long long)l0 * nb * h->ldH : Htmp;
       dim3 ge(256, nbt);
       extract_kernel<double2><<<ge, 256, 0, st>>>(W, wstride, ld, n, ni, nb, h->eta, nbt, Rb,
                                                   (long long)nb * h->ldR, h->ldR, Hb, (long long)nb * h->ldH, h->ldH);
@@ -825,6 +848,11 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
         cast_kernel<<<1024, 256, 0, st>>>(Rb, h->R32 + (long long)l0 * nb * h->ldR, cnt);
         HPS_CUDA_TRY(cudaGetLastError());
       }
+      if (h->H32) {
+        const long long cnt = (long long)nbt * nb * h->ldH;
+        cast_kernel<<<1024, 256, 0, st>>>(Hb, h->H32 + (long long)l0 * nb * h->ldH, cnt);
+        HPS_CUDA_TRY(cudaGetLastError());
+      }
       return HPS_OK;
     };
     rc = body();
@@ -833,6 +861,8 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
   cudaStreamSynchronize(st);
   cudaFree(W);
   cudaFree(d_status);
+  if (Rtmp) cudaFree(Rtmp);
+  if (Htmp) cudaFree(Htmp);
   return rc;
 }
 
@@ -955,9 +985,18 @@ int build_precond_blocks(hps_handle* h, const double2* cdiag, const int* d_cl_le
                               d_status, st));
         cstart = cend;
       }
-      extract_kc_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
-                                                          h->dct.cl_kc_off, q, h->Kc64, h->Kc32);
-      HPS_CUDA_TRY(cudaGetLastError());
+      if (h->Kc64 || h->Kc32) {
+        extract_kc_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
+                                                            h->dct.cl_kc_off, q, h->Kc64, h->Kc32);
+        HPS_CUDA_TRY(cudaGetLastError());
+      }
+      if constexpr (std::is_same<T, float2>::value) {
+        if (!h->Kc32 && h->Kc16) {
+          quantize_kc_ws_kernel<<<dim3(64, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
+                                                              h->dct.cl_kc_off, q2, h->Kc16, h->Kc16s);
+          HPS_CUDA_TRY(cudaGetLastError());
+        }
+      }
       return HPS_OK;
     };
     rc = body();

@@ -12,8 +12,8 @@
 // the face-vector layout and rewritten in shared memory.
 //
 // Precision: three TF32 products (A_hi B_hi + A_hi B_lo + A_lo B_hi, with
-// x_hi = x with its low 13 mantissa bits cleared and x_lo = x - x_hi) give
-// about FP32 accuracy; FP32 accumulation in tensor memory (TMEM).
+// x_hi = x rounded to TF32 and x_lo = x - x_hi rounded to TF32) keep about 22
+// bits per product term; FP32 accumulation in tensor memory (TMEM).
 //
 // Kernel (one CTA per SM, persistent over items = (leaf, 128-row tile)):
 //   warp 0       TMA producer: A tile (128 rows x 32 floats) and F tile
@@ -139,7 +139,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (10 explicit mantissa bits, ties away from zero)
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 
 // 32 consecutive accumulator columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float4 v = Ahi[c];
           const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
           Ahi[c] = h;
-          Alo[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+          Alo[c] = make_float4(tf32_hi(v.x - h.x), tf32_hi(v.y - h.y), tf32_hi(v.z - h.z), tf32_hi(v.w - h.w));
         }
         // F rows s (64 x 128 bytes): B row s = conj(f_s), B row 64+s = swap(f_s); the
         // 16-byte chunk positions (and so the swizzle) are the same in both halves.
@@ -264,9 +269,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float4 cjh = make_float4(tf32_hi(cj.x), tf32_hi(cj.y), tf32_hi(cj.z), tf32_hi(cj.w));
           const float4 swh = make_float4(tf32_hi(sw.x), tf32_hi(sw.y), tf32_hi(sw.z), tf32_hi(sw.w));
           Bhi[c] = cjh;
-          Blo[c] = make_float4(cj.x - cjh.x, cj.y - cjh.y, cj.z - cjh.z, cj.w - cjh.w);
+          Blo[c] = make_float4(tf32_hi(cj.x - cjh.x), tf32_hi(cj.y - cjh.y), tf32_hi(cj.z - cjh.z),
+                               tf32_hi(cj.w - cjh.w));
           Bhi[c + kFBytes / 16] = swh;
-          Blo[c + kFBytes / 16] = make_float4(sw.x - swh.x, sw.y - swh.y, sw.z - swh.z, sw.w - swh.w);
+          Blo[c + kFBytes / 16] = make_float4(tf32_hi(sw.x - swh.x), tf32_hi(sw.y - swh.y), tf32_hi(sw.z - swh.z),
+                                              tf32_hi(sw.w - swh.w));
         }
         // make the generic-proxy writes visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -446,7 +453,7 @@ cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool 
       return cudaErrorInvalidValue;
   }
   const int smem = kStages * kStageBytes + (int)sizeof(Bars) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(tc_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = allow_dynamic_smem((const void*)tc_apply_kernel, smem);
   if (e != cudaSuccess) return e;
   for (int r0 = 0; r0 < nrhs; r0 += kRhs) {
     CUtensorMap mapF;

@@ -1,0 +1,158 @@
+"""Accuracy experiment of Sec. 6.2 (Table PlaneMinErr) on one GPU.
+
+The test solution u = e^{i kappa (x+y+z)} e^x cosh(y) (z+1)^2 with the Gaussian
+bump medium b = -1.5 exp(-160|x - 0.5|^2) is solved with n_c = 16 Chebyshev
+points per leaf axis (q = 14 Gauss points per face edge) at a fixed number of
+points per wavelength.  The wave number follows the tables of Sec. 6.1: a grid
+of L leaves per axis at `ppw` points per wavelength spans 12 L / ppw
+wavelengths (16 ppw on 4^3 leaves = 3 wavelengths), kappa = 2 pi 12 L / ppw.
+The solve runs in FP64 to stagnation and E_h is the relative l2 error of the
+recovered leaf solutions at the interior nodes.
+
+    python -m paper_2112_02211_gb300.experiments [--L 4] [--ppw 24 16 9.6]
+    python -m paper_2112_02211_gb300.experiments --large
+    python -m paper_2112_02211_gb300.experiments --multi-rhs [--L 16]
+"""
+
+import argparse
+import json
+import math
+
+import numpy as np
+
+
+def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
+    import torch
+
+    import workloads as W
+
+    from . import Solver, face_normals, nodes
+    kappa = 2.0 * math.pi * 12.0 * L / ppw
+    w = W.manufactured(L=L, p=p, kappa=kappa)
+    xi, xf = nodes(L, L, L, p)
+    nrm = np.broadcast_to(face_normals()[None, :, None, :], xf.shape)
+    s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
+    t = torch.from_numpy(w.sample_t(xf, nrm).reshape(-1)).cuda()
+    solver = Solver(L, L, L, p, kappa=kappa, eta=kappa, b=w.sample_b(xi), forms=("fp64",), cluster=0)
+    try:
+        f, info = solver.solve(s=s, t=t, tol=tol, form="fp64")
+        u = solver.recover(f, s=s).cpu().numpy()
+    finally:
+        solver.close()
+    u_exact = w.meta["u"](xi).reshape(-1)
+    e_h = float(np.linalg.norm(u - u_exact) / np.linalg.norm(u_exact))
+    return {"leaves": L, "ppw": ppw, "kappa": kappa, "E_h": e_h, "iterations": info["iterations"],
+            "rel_residual": info["rel_residual"]}
+
+
+def large_solve(L=32, steps=3, warmup=1):
+    """The large single solve: 32^3 leaves, p = 10, kappa = eta = 200, smooth random complex
+    medium, Gaussian source of width 0.01 at the centre, tol 1e-5, lean mixed form (FP32 maps,
+    FP16 cluster inverses, double-float Krylov basis).  Returns setup time, memory and the
+    per-solve time, iterations and throughput (face unknowns/s), inputs resident on the GPU."""
+    import time
+
+    import torch
+
+    import workloads as W
+
+    from . import Solver, nodes
+    w = W.large_32cubed(L=L)
+    xi, xf = nodes(L, L, L, w.p)
+    b = w.sample_b(xi)
+    s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
+    t0 = time.time()
+    solver = Solver(L, L, L, w.p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",), lean=True)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    try:
+        out = torch.empty(solver.nf, dtype=torch.complex128, device="cuda")
+        for _ in range(warmup):
+            solver.solve(s=s, tol=w.tol, form="mixed", out=out)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        solver.profile(enable=True, reset=True)
+        e0.record()
+        for _ in range(steps):
+            _, info = solver.solve(s=s, tol=w.tol, form="mixed", out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = solver.profile(enable=False, reset=True)
+        mem = solver.memory_bytes
+    finally:
+        solver.close()
+    return {"workload": f"large_{L}cubed", "leaves": L ** 3, "face_unknowns": solver.nf, "setup_s": setup_s,
+            "device_bytes": mem, "ms_per_solve": ms, "unknowns_per_s": solver.nf / (ms / 1e3),
+            "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+            "phase_ms_per_solve": {k: v / steps for k, v in prof["ms"].items()}}
+
+
+def multi_rhs(L=16, nrhs=64, restart=30, steps=2, warmup=1, precond=False):
+    """The multi-RHS workload: L^3 leaves, p = 12 (q = 10, leaf ItI 600 x 600), kappa = eta = 60,
+    five seeded bumps, 64 Gaussian sources of width 0.02, tol 1e-6; lean mixed form with the
+    apply of all 64 right-hand sides on the tensor cores (tcgen05, three TF32 products).
+    Restart 30 keeps the 64-RHS Krylov basis at 31 x 64 x N_f complex double-floats."""
+    import time
+
+    import torch
+
+    import workloads as W
+
+    from . import Solver, nodes
+    w = W.multi_rhs_16cubed(L=L, nrhs=nrhs)
+    xi, xf = nodes(L, L, L, w.p)
+    s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
+    t0 = time.time()
+    solver = Solver(L, L, L, w.p, kappa=w.kappa, eta=w.eta, b=w.sample_b(xi), forms=("mixed",), lean=True,
+                    restart=restart, max_rhs=nrhs, cluster=2 if precond else 0)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    try:
+        out = torch.empty(nrhs * solver.nf, dtype=torch.complex128, device="cuda")
+        for _ in range(warmup):
+            solver.solve(s=s, tol=w.tol, form="mixed", out=out, nrhs=nrhs)
+        solver.profile(enable=True, reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            _, info = solver.solve(s=s, tol=w.tol, form="mixed", out=out, nrhs=nrhs)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = solver.profile(enable=False, reset=True)
+        nb, q2 = solver.nb, solver.q * solver.q
+    finally:
+        solver.close()
+    napply = prof["count"]["apply"]
+    apply_ms = prof["ms"]["apply"] / max(1, napply)
+    r_bytes = L ** 3 * nb * nb * 8
+    flops = 8.0 * L ** 3 * nb * nb * nrhs
+    return {"workload": f"multi_rhs_{L}cubed", "nrhs": nrhs, "face_unknowns_per_rhs": solver.nf,
+            "setup_s": setup_s, "ms_per_solve": ms, "unknowns_per_s": nrhs * solver.nf / (ms / 1e3),
+            "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+            "apply_ms": apply_ms, "apply_R_GBps": r_bytes / (apply_ms / 1e3) / 1e9,
+            "apply_complex_TFLOPs": flops / (apply_ms / 1e3) / 1e12,
+            "phase_ms_per_solve": {k: v / steps for k, v in prof["ms"].items()}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, default=4)
+    ap.add_argument("--ppw", type=float, nargs="*", default=[24.0, 19.2, 16.0, 12.0, 9.6])
+    ap.add_argument("--large", action="store_true", help="run the 32^3-leaf large solve instead")
+    ap.add_argument("--multi-rhs", action="store_true", help="run the 64-RHS tensor-core workload instead")
+    args = ap.parse_args()
+    if args.large:
+        print(json.dumps(large_solve()), flush=True)
+        return
+    if args.multi_rhs:
+        print(json.dumps(multi_rhs(L=args.L if args.L != 4 else 16)), flush=True)
+        return
+    for ppw in args.ppw:
+        print(json.dumps(plane_min_err(L=args.L, ppw=ppw)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

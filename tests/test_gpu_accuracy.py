@@ -1,0 +1,33 @@
+"""The paper's accuracy experiment (Sec. 6.2, Table PlaneMinErr) at n_c = 16 on
+4^3 leaves: E_h of the recovered solution within an order of magnitude of the
+printed value (the mapping from points per wavelength to kappa is a reading of
+the tables of Sec. 6.1, and E_h here is taken at the interior nodes)."""
+
+import math
+import os
+
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2112_02211_gb300.experiments import plane_min_err  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_plane_min_err.txt")
+
+
+def _printed():
+    vals = {}
+    for line in open(GOLDEN):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            a, b = line.split()
+            vals[float(a)] = float(b)
+    return vals
+
+
+@pytest.mark.parametrize("ppw", [24.0, 9.6])
+def test_plane_min_err_order_of_magnitude(ppw):
+    printed = _printed()[ppw]
+    r = plane_min_err(L=4, p=16, ppw=ppw)
+    assert abs(math.log10(r["E_h"] / printed)) <= 1.0, r

@@ -122,6 +122,24 @@ def test_mixed_only_handle_builds_fp32_preconditioner(ragged):
         solver.close()
 
 
+def test_lean_mode_solve(ragged):
+    """Lean mode: FP32 maps only, FP16 cluster inverses, residual with FP32 maps against
+    FP64 vectors; the solution meets a 1e-5 tolerance against the oracle."""
+    w, oc, _, (xi, xf, b, s, t) = ragged
+    solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",), lean=True)
+    try:
+        f, info = solver.solve(s=torch.from_numpy(s.reshape(-1)).cuda(), t=torch.from_numpy(t.reshape(-1)).cuda(),
+                               tol=1e-7, form="mixed")
+        assert info["converged"], info
+        assert rel(f.cpu().numpy(), oc.solve()) < 1e-5
+        R = solver.export("R", 3).reshape(oc.grid.nb, oc.grid.nb)
+        assert rel(R, oc.prob.R[3]) < 1e-6
+        with pytest.raises(hps.HPSError):
+            solver.apply(torch.zeros(oc.grid.nf, dtype=torch.complex128, device="cuda"))
+    finally:
+        solver.close()
+
+
 def test_rhs_matches_oracle(ragged):
     w, oc, solver, (xi, xf, b, s, t) = ragged
     bg = solver.rhs(torch.from_numpy(s.reshape(-1)).cuda(), torch.from_numpy(t.reshape(-1)).cuda())
