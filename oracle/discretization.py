@@ -29,7 +29,7 @@ __all__ = [
     "FACE_AXIS", "FACE_SIGN", "IN_FACE_AXES",
     "chebyshev_lobatto", "chebyshev_diff", "gauss_legendre", "lagrange_matrix",
     "LeafLayout", "Grid", "leaf_matrix", "leaf_maps", "face_interp",
-    "leaf_iti", "interior_nodes", "face_nodes", "face_normals",
+    "leaf_iti", "interior_nodes", "face_nodes", "cheb_face_nodes", "face_normals",
     "homogenized_lambda", "binned_lambdas", "leaf_incoming_op", "leaf_outgoing_op",
 ]
 
@@ -212,6 +212,28 @@ def face_nodes(grid):
                     pt[a0] = c[a0] + 0.5 * grid.h[a0] * (xg[j1] + 1.0)
                     pt[a1] = c[a1] + 0.5 * grid.h[a1] * (xg[j2] + 1.0)
                     out[leaf, face, j1 + q * j2] = pt
+    return out
+
+
+def cheb_face_nodes(grid):
+    """Coordinates of the n1 x n1 Chebyshev nodes of every leaf face (the face
+    part of the leaf grid, Sec. 2.1 and Fig. 2), shape (N_l, 6, n1^2, 3), in the
+    order of LeafLayout's face nodes."""
+    n1 = grid.p - 2
+    x = chebyshev_lobatto(grid.p)
+    out = np.zeros((grid.nleaves, 6, n1 * n1, 3))
+    for leaf in range(grid.nleaves):
+        c = grid.corner(leaf)
+        for face in range(6):
+            axis = FACE_AXIS[face]
+            a0, a1 = IN_FACE_AXES[face]
+            for j2 in range(n1):
+                for j1 in range(n1):
+                    pt = np.zeros(3)
+                    pt[axis] = c[axis] + (0.0 if FACE_SIGN[face] < 0 else grid.h[axis])
+                    pt[a0] = c[a0] + 0.5 * grid.h[a0] * (x[j1 + 1] + 1.0)
+                    pt[a1] = c[a1] + 0.5 * grid.h[a1] * (x[j2 + 1] + 1.0)
+                    out[leaf, face, j1 + n1 * j2] = pt
     return out
 
 

@@ -124,16 +124,18 @@ def rhs_face(grid, H, s_int, t_face):
     return b
 
 
-def recover_interior(grid, kappa, eta, b_int, s_int, f_face):
+def recover_interior(grid, kappa, eta, b_int, s_int, f_face, with_faces=False):
     """Leaf solution at interior nodes from face data (eq. (leaf)):
     u^tau = A^{tau,-1} [s^tau; P^{-1} f^tau], f^tau moved from Gauss points to the
-    Chebyshev face nodes by P^{-1}.  Returns (N_l, n_i)."""
+    Chebyshev face nodes by P^{-1}.  Returns (N_l, n_i), and with with_faces
+    also the leaf solution at its Chebyshev face nodes (N_l, n_b)."""
     from .discretization import face_interp, leaf_matrix
     L = grid.layout
     Pf = face_interp(grid.p)
     q2 = grid.q * grid.q
     f = np.asarray(f_face).reshape(grid.nleaves, 6, q2)
     u = np.zeros((grid.nleaves, L.ni), dtype=np.complex128)
+    ub = np.zeros((grid.nleaves, L.nb), dtype=np.complex128)
     b_int = np.asarray(b_int).reshape(grid.nleaves, -1)
     for leaf in range(grid.nleaves):
         A = leaf_matrix(grid.p, grid.h, eta, cdiag_from_b(kappa, b_int[leaf]))
@@ -142,8 +144,10 @@ def recover_interior(grid, kappa, eta, b_int, s_int, f_face):
             rhs[:L.ni] = np.asarray(s_int).reshape(grid.nleaves, -1)[leaf]
         for face in range(6):
             rhs[L.ni + face * q2:L.ni + (face + 1) * q2] = np.linalg.solve(Pf, f[leaf, face])
-        u[leaf] = np.linalg.solve(A, rhs)[:L.ni]
-    return u
+        sol = np.linalg.solve(A, rhs)
+        u[leaf] = sol[:L.ni]
+        ub[leaf] = sol[L.ni:]
+    return (u, ub) if with_faces else u
 
 
 def dense_face_matrix(grid, R):

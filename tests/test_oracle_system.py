@@ -80,6 +80,29 @@ def test_recovered_interior_solution_converges():
     assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10
 
 
+def test_recovered_face_values_match_the_solution_at_chebyshev_face_nodes():
+    """The face part of u = A^{-1}[s; P^{-1} f] is u at the Chebyshev face nodes (the rest
+    of the paper's unknowns): spectral convergence to the manufactured u there, and
+    leaves sharing a face agree on it."""
+    errs = []
+    for p in (6, 8, 10):
+        w = W.manufactured(L=2, p=p, kappa=8.0)
+        grid, prob, rhs, (xi, xf, nrm, b, s, t) = _setup(w)
+        f = np.linalg.solve(O.dense_face_matrix(grid, prob.R), rhs)
+        u, ub = O.recover_interior(grid, w.kappa, w.eta, b, s[0], f, with_faces=True)
+        xc = O.cheb_face_nodes(grid)
+        errs.append(O.relative_error(ub, w.meta["u"](xc)))
+        ub = ub.reshape(grid.nleaves, 6, -1)
+        for leaf in range(grid.nleaves):
+            for face in range(6):
+                nbr = grid.neighbor(leaf, face)
+                if nbr >= 0:
+                    assert np.allclose(xc[leaf, face], xc[nbr, face ^ 1], atol=1e-15)
+                    assert O.relative_error(ub[leaf, face], ub[nbr, face ^ 1]) < 10 * errs[-1]
+    assert errs[-1] < 1e-4
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10
+
+
 def test_dense_solve_matches_gmres_and_preconditioned_gmres():
     w = W.manufactured(L=2, p=6, kappa=12.0)
     w.ny = 2
