@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--cpu-sample-L", type=int, default=4)
     ap.add_argument("--serving-requests", type=int, default=8,
                     help="requests of the scaled serving stream timed after the solves (0 = skip)")
+    ap.add_argument("--lambda-bin", type=float, default=0.01,
+                    help="bin width of the homogenized constants, relative to max |lambda| (0 = per-leaf)")
+    ap.add_argument("--no-unbinned", action="store_true",
+                    help="skip the comparison solve with per-leaf (unbinned) preconditioner blocks")
     return ap.parse_args()
 
 
@@ -166,17 +170,31 @@ def apply_bytes(L, q, mat_bytes, in_bytes, out_bytes):
     return interior_face_pairs(L) * q * q * nb * mat_bytes + nf * (2 * in_bytes + out_bytes)
 
 
-def precond_bytes(L, q, mat_bytes, vec_bytes, in_bytes=None, scale_bytes=0):
-    """Stage K: K_c of every 2x2x2 cluster (+ one row scale for FP16 blocks) + t read + z_int
-    write.  Stage B: B blocks (+ row scales) + r read once + t and z_ext written."""
+def precond_bytes(L, q, mat_bytes, vec_bytes, in_bytes=None, scale_bytes=0, k_blocks=None, b_blocks=None):
+    """Stage K: every distinct K_c block once (+ one row scale per row for FP16 blocks) + t read +
+    z_int write per cluster.  Stage B: every distinct B block once (+ row scales) + r read once +
+    t and z_ext written.  Without sharing k_blocks = clusters, b_blocks = leaves.  L even."""
     in_bytes = vec_bytes if in_bytes is None else in_bytes
     q2 = q * q
     ncl = (L // 2) ** 3
+    k_blocks = ncl if k_blocks is None else k_blocks
+    b_blocks = L ** 3 if b_blocks is None else b_blocks
     nint = 24 * q2
-    kb = ncl * nint * (nint * mat_bytes + scale_bytes) + ncl * nint * 2 * vec_bytes
+    kb = k_blocks * nint * (nint * mat_bytes + scale_bytes) + ncl * nint * 2 * vec_bytes
     nf = L ** 3 * 6 * q2
-    bb = L ** 3 * (3 * q2) * (3 * q2 * mat_bytes + scale_bytes) + nf * in_bytes + nf * vec_bytes
+    bb = b_blocks * (3 * q2) * (3 * q2 * mat_bytes + scale_bytes) + nf * in_bytes + nf * vec_bytes
     return kb, bb
+
+
+def precond_k_flops(L, q):
+    """Stage K: one complex multiply-add (8 real flops) per K_c entry per cluster."""
+    nint = 24 * q * q
+    return 8.0 * (L // 2) ** 3 * nint * nint
+
+
+def fp32_peak_tflops(sm_mhz, sms=152):
+    """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def peaks():
@@ -220,9 +238,10 @@ def run_gpu(args, dist):
     b = w.sample_b(xi)
     s = w.sample_s(xi).reshape(-1)
     t0 = time.time()
-    solver = hps.Solver(L, L, L, p, kappa=w.kappa, eta=w.eta, b=b, device=dist.local)
+    solver = hps.Solver(L, L, L, p, kappa=w.kappa, eta=w.eta, b=b, device=dist.local, lambda_bin=args.lambda_bin)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
+    ncl, k_blocks, b_blocks = solver.precond_info()
     nf = solver.nf
     s_dev = torch.from_numpy(s).cuda()
     out = torch.empty(nf, dtype=torch.complex128, device="cuda")
@@ -286,6 +305,17 @@ def run_gpu(args, dist):
                 compare[key]["mixed_vs_fp64_rel_diff"] = float(
                     torch.linalg.norm(f_mixed - out).item() / torch.linalg.norm(out).item())
 
+    # per-leaf (unbinned) preconditioner blocks, mixed form, for comparison
+    if not args.no_compare and not args.no_unbinned and args.lambda_bin > 0:
+        solver.close()
+        solver = hps.Solver(L, L, L, p, kappa=w.kappa, eta=w.eta, b=b, device=dist.local, forms=("mixed",))
+        c_ms, c_infos, c_prof, _ = timed("mixed", True, 1, 1, profile=True)
+        compare["mixed_unbinned"] = {
+            "unknowns_per_s": nf / (c_ms / 1e3), "ms_per_solve": c_ms, "iterations": c_infos[-1]["iterations"],
+            "rel_residual": c_infos[-1]["rel_residual"], "k_blocks": solver.precond_info()[1],
+            "phase_ms": {k: round(v, 3) for k, v in c_prof["ms"].items()},
+            "rel_diff_vs_headline": float(torch.linalg.norm(f_mixed - out).item() / torch.linalg.norm(out).item())}
+
     # roofline of the dominant kernel and of the ItI apply, from the library's events
     pk, pk_src = peaks()
     q2 = q * q
@@ -293,11 +323,12 @@ def run_gpu(args, dist):
     a_bytes = apply_bytes(L, q, 8, 8, 16)
     # FP16 blocks (4 bytes per complex entry + a 4-byte scale per row), c64 vectors,
     # double-float (16-byte) input to stage B
-    kb, bb = precond_bytes(L, q, 4, 8, in_bytes=16, scale_bytes=4)
+    kb, bb = precond_bytes(L, q, 4, 8, in_bytes=16, scale_bytes=4, k_blocks=k_blocks, b_blocks=b_blocks)
     phases = {"apply": a_bytes, "precond_k": kb, "precond_b": bb}
     kernels = {"apply": "seg_gemv_kernel<ApplyP<float2,float2,float4>,1,4>",
-               "precond_k": "seg_gemv_kernel<PrecKP<__half2,float2,float2>,1,4>",
+               "precond_k": "seg_gemv_kernel<PrecKP<__half2,float2,float2>,W,R> (W = 1, 2, 4, 8 clusters per block)",
                "precond_b": "seg_gemv_kernel<PrecBP<__half2,float4,float2>,1,4>"}
+    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
     roof = {}
     for ph, by in phases.items():
         cnt = prof["count"][ph]
@@ -308,6 +339,16 @@ def run_gpu(args, dist):
                         "frac": round(ach / pk, 4), "traffic": committed_traffic(ph),
                         "algorithmic_bytes": by, "avg_launch_ms": round(dur * 1e3, 4), "launches": cnt,
                         "kernel": kernels[ph], "peak_source": pk_src}
+            if ph == "precond_k":
+                # shared blocks make stage K a grouped complex GEMM: bound by the FP32 pipe when
+                # its flop time exceeds its byte time
+                fl = precond_k_flops(L, q)
+                fpk = fp32_peak_tflops(sm_mhz)
+                if fl / (fpk * 1e12) > by / (pk * 1e9):
+                    ach_f = fl / dur / 1e12
+                    roof[ph].update({"bound": "alu", "achieved": round(ach_f, 2), "peak": round(fpk, 1),
+                                     "unit": "TFLOP/s", "frac": round(ach_f / fpk, 4), "algorithmic_flops": fl,
+                                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops at {sm_mhz:g} MHz"})
     dominant = max(roof, key=lambda k: prof["ms"][k]) if roof else None
     iters = infos[-1]["iterations"]
     rec = {
@@ -329,6 +370,8 @@ def run_gpu(args, dist):
             "form": "mixed (complex-FP32 apply and preconditioner, CGS2 Arnoldi in double-float "
                     "(FP64-accurate, FP32 pipe), FP64 restart residual)",
             "preconditioner": "2x2x2 cluster block Jacobi, homogenized leaf maps, blocks in FP16 with FP32 row scales",
+            "lambda_bin": args.lambda_bin,
+            "precond_blocks": {"clusters": ncl, "distinct_K": k_blocks, "distinct_B": b_blocks},
             "restart": 50,
             "face_unknowns": nf,
             "paper_unknowns": L ** 3 * ((p - 2) ** 3 + 6 * (p - 2) ** 2),

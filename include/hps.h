@@ -91,13 +91,23 @@ typedef struct {
   int device;         /* CUDA device ordinal */
   int precond_fp16;   /* mixed form: also keep the preconditioner blocks in FP16 with one FP32
                          scale per row and use them in hps_gmres_solve (default 1) */
-  int tc_apply;       /* complex-FP32 apply of 64, 128, ... right-hand sides on the tensor cores
-                         (three TF32 products, FP32 accumulation; default 1) */
+  int tc_apply;       /* tensor cores (three TF32 products, FP32 accumulation) for the
+                         complex-FP32 apply of 64, 128, ... right-hand sides and for
+                         preconditioner blocks shared by >= 16 clusters (complex-FP32
+                         blocks; see lambda_bin); default 1 */
   int lean;           /* memory-lean mixed form (forms must be HPS_FORM_MIXED): the exact leaf
                          maps R, H are eliminated in FP64 but kept only in FP32, the cluster
                          inverses only in FP16, and the restart residual uses the FP32 maps with
                          FP64 vectors (about 1e-7 relative per apply, for tolerances >= 1e-5).
                          HPS_C128 applies are then unavailable.  Default 0. */
+  double lambda_bin;  /* shared preconditioner blocks (Sec. 4.1 remark: one local solver for
+                         leaves with nearly the same medium): each lambda^tau is rounded to the
+                         nearest multiple of lambda_bin * max_tau |lambda^tau| (real and imaginary
+                         parts separately, ties to even) before R~ and K_c are built, and clusters
+                         whose leaves carry equal values in the same arrangement share one K_c
+                         (leaves: one B block).  0 (default) keeps every lambda^tau; blocks are
+                         still shared where values are bitwise equal.  Finite, >= 0.  Changes the
+                         preconditioner only, never the converged solution. */
 } hps_options;
 
 typedef struct {
@@ -113,11 +123,15 @@ void hps_default_options(hps_options* opt);
 
 /*
  * Node coordinates of a grid, computed on the device (Sec. 2.1).
- * interior_xyz: host, nx*ny*nz*n1^3*3 doubles (x,y,z per node, layout above),
- * face_xyz:     host, N_f*3 doubles, the Gauss points of every leaf face.
- * Either pointer may be NULL.  Uses the current CUDA device.
+ * interior_xyz:   host, nx*ny*nz*n1^3*3 doubles (x,y,z per node, layout above),
+ * face_xyz:       host, N_f*3 doubles, the Gauss points of every leaf face,
+ * cheb_face_xyz:  host, N_f*3 doubles, the leaf's Chebyshev face nodes (the
+ *                 n1 x n1 interior points of each face, face layout above
+ *                 with j1/j2 indexing Chebyshev points) where hps_recover
+ *                 returns face values.
+ * Any pointer may be NULL.  Uses the current CUDA device.
  */
-int hps_nodes(const hps_grid* grid, double* interior_xyz, double* face_xyz);
+int hps_nodes(const hps_grid* grid, double* interior_xyz, double* face_xyz, double* cheb_face_xyz);
 
 /*
  * Builds the leaf ItI maps R^tau (Gauss basis), the body-load maps H^tau and
@@ -212,15 +226,25 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
                     double tol, double* f_out, hps_solve_info* info, void* stream);
 
 /*
- * Leaf solutions at the interior nodes from face data (eq. (leaf)):
+ * Leaf solutions from face data (eq. (leaf)):
  * u^tau = A^{tau,-1} [s^tau; P^{-1} f^tau], P^{-1} moving the Gauss-point face
  * data to the leaf's Chebyshev face nodes.  s: nrhs interior vectors or NULL
  * (s = 0); f: nrhs face vectors (typically the output of hps_gmres_solve);
- * u_out: nrhs interior vectors (layout of hps_nodes' interior points).  All
+ * u_out: nrhs interior vectors (layout of hps_nodes' interior points);
+ * u_face_out: NULL or nrhs face-layout vectors of u at the Chebyshev face
+ * nodes (hps_nodes' cheb_face_xyz), the rest of the leaf's unknowns.  All
  * device pointers, complex double; one FP64 elimination per leaf and call
  * (cost comparable to hps_setup's).  Synchronous.
  */
-int hps_recover(hps_handle* h, const double* s, const double* f, int nrhs, double* u_out, void* stream);
+int hps_recover(hps_handle* h, const double* s, const double* f, int nrhs, double* u_out,
+                double* u_face_out, void* stream);
+
+/*
+ * Distinct preconditioner blocks of the handle: clusters, distinct K_c blocks
+ * and distinct B blocks (see hps_options.lambda_bin).  Any pointer may be NULL.
+ * HPS_EINVAL when the handle has no preconditioner.
+ */
+int hps_precond_info(const hps_handle* h, int* clusters, int* k_blocks, int* b_blocks);
 
 /* What hps_export copies out (host doubles, interleaved complex). */
 #define HPS_EXPORT_R 0      /* R^index, 6q^2 x 6q^2 row-major, FP64 */

@@ -39,16 +39,19 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def nodes(nx, ny, nz, p):
-    """Interior Chebyshev nodes (nl, n1^3, 3) and face Gauss points (nl, 6, q^2, 3), from the device."""
+def nodes(nx, ny, nz, p, cheb_faces=False):
+    """Interior Chebyshev nodes (nl, n1^3, 3) and face Gauss points (nl, 6, q^2, 3), from the device;
+    with cheb_faces also the Chebyshev face nodes (nl, 6, n1^2, 3) of `Solver.recover(faces=True)`."""
     lib = N.load()
     q = p - 2
     nl = nx * ny * nz
     xi = np.zeros((nl, (p - 2) ** 3, 3))
     xf = np.zeros((nl, 6, q * q, 3))
+    xc = np.zeros((nl, 6, q * q, 3)) if cheb_faces else None
     g = N.Grid(nx, ny, nz, p, q)
-    N.check(lib.hps_nodes(ctypes.byref(g), xi.ctypes.data_as(ctypes.c_void_p), xf.ctypes.data_as(ctypes.c_void_p)))
-    return xi, xf
+    N.check(lib.hps_nodes(ctypes.byref(g), xi.ctypes.data_as(ctypes.c_void_p), xf.ctypes.data_as(ctypes.c_void_p),
+                          None if xc is None else xc.ctypes.data_as(ctypes.c_void_p)))
+    return (xi, xf, xc) if cheb_faces else (xi, xf)
 
 
 def face_normals():
@@ -67,7 +70,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, p, kappa, eta=None, b=None, forms=("fp64", "mixed"), restart=50,
                  cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0, precond_fp16=True, tc_apply=True,
-                 lean=False):
+                 lean=False, lambda_bin=0.0):
         self.lib = N.load()
         self.nx, self.ny, self.nz, self.p, self.q = nx, ny, nz, p, p - 2
         self.nl = nx * ny * nz
@@ -90,6 +93,7 @@ class Solver:
         opt.precond_fp16 = 1 if precond_fp16 else 0
         opt.tc_apply = 1 if tc_apply else 0
         opt.lean = 1 if lean else 0
+        opt.lambda_bin = float(lambda_bin)
         bb = None
         if b is not None:
             bb = np.ascontiguousarray(np.asarray(b, dtype=np.complex128).reshape(-1))
@@ -167,13 +171,21 @@ class Solver:
              "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc}
         return out, d
 
-    def recover(self, f, s=None, nrhs=None, stream=None):
-        """Leaf solutions at the interior nodes, u = A^{-1}[s; P^{-1} f] per leaf (device tensors)."""
+    def recover(self, f, s=None, nrhs=None, stream=None, faces=False):
+        """Leaf solutions at the interior nodes, u = A^{-1}[s; P^{-1} f] per leaf (device tensors);
+        with faces=True also u at the Chebyshev face nodes (face layout)."""
         torch = _torch()
         nrhs = nrhs or self._nrhs(f)
         u = torch.empty(nrhs * self.nl * self.ni, dtype=torch.complex128, device="cuda")
-        N.check(self.lib.hps_recover(self.handle, _ptr(s), _ptr(f), nrhs, _ptr(u), _stream(stream)))
-        return u
+        uf = torch.empty(nrhs * self.nf, dtype=torch.complex128, device="cuda") if faces else None
+        N.check(self.lib.hps_recover(self.handle, _ptr(s), _ptr(f), nrhs, _ptr(u), _ptr(uf), _stream(stream)))
+        return (u, uf) if faces else u
+
+    def precond_info(self):
+        """(clusters, distinct K_c blocks, distinct B blocks) of the preconditioner."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        N.check(self.lib.hps_precond_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def export(self, what, index):
         """Copy one stored operator block to the host (numpy complex128)."""

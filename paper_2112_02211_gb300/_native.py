@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
     _fields_ = [("forms", ctypes.c_int), ("restart", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("max_rhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
                 ("device", ctypes.c_int), ("precond_fp16", ctypes.c_int), ("tc_apply", ctypes.c_int),
-                ("lean", ctypes.c_int)]
+                ("lean", ctypes.c_int), ("lambda_bin", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -57,7 +57,7 @@ _D = ctypes.POINTER(ctypes.c_double)
 
 SIGNATURES = {
     "hps_default_options": (None, [ctypes.POINTER(Options)]),
-    "hps_nodes": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P]),
+    "hps_nodes": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _P]),
     "hps_setup": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_double, _P,
                                  ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "hps_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
@@ -66,8 +66,10 @@ SIGNATURES = {
     "hps_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
     "hps_gmres_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P,
                                        ctypes.POINTER(SolveInfo), _P]),
-    "hps_recover": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
+    "hps_recover": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "hps_export": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "hps_precond_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
     "hps_memory_bytes": (ctypes.c_size_t, [_P]),
     "hps_setup_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), ctypes.POINTER(Options), ctypes.c_int]),
     "hps_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),

@@ -110,10 +110,12 @@ void free_handle(hps_handle* h) {
   cudaSetDevice(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
   krylov_free(h);
-  void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->H32, h->lambda, h->Kc64, h->Kc32, h->B64, h->B32, h->pc_scratch,
-                  h->Kc16, h->Kc16s, h->B16, h->B16s, h->tc_error, h->cdiag,
+  void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->H32, h->lambda, h->lambda_q, h->Kc64, h->Kc32, h->B64,
+                  h->B32, h->pc_scratch, h->Kc16, h->Kc16s, h->B16, h->B16s, h->tc_error, h->cdiag,
                   h->dct.slot_lf, h->dct.slot_cluster, h->dct.cl_slot_begin, h->dct.cl_kc_off, h->dct.lf_slot,
-                  h->dct.int_mask, h->dct.b_off};
+                  h->dct.int_mask, h->dct.b_off, h->dct.leaf_bcls, h->dct.bc_rep, h->dct.kc_off,
+                  h->dct.kc_slot_begin, h->dct.kslot_class, h->dct.kc_members, h->dct.kitems[0], h->dct.kitems[1],
+                  h->dct.kitems[2], h->dct.kitems[3], h->dct.cl_tpos, h->dct.lf_tpos};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -162,6 +164,10 @@ int check_options(const hps_options& o) {
     set_error("lean mode keeps FP32 maps only: forms must be HPS_FORM_MIXED");
     return HPS_EINVAL;
   }
+  if (!std::isfinite(o.lambda_bin) || o.lambda_bin < 0.0) {
+    set_error("lambda_bin must be finite and >= 0");
+    return HPS_EINVAL;
+  }
   return HPS_OK;
 }
 
@@ -190,30 +196,34 @@ void hps_default_options(hps_options* o) {
   o->precond_fp16 = 1;
   o->tc_apply = 1;
   o->lean = 0;
+  o->lambda_bin = 0.0;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
 
-int hps_nodes(const hps_grid* g, double* xi, double* xf) {
+int hps_nodes(const hps_grid* g, double* xi, double* xf, double* xc) {
   int rc = validate_grid(g);
   if (rc) return rc;
   TableLayout tl(g->p);
   const long long nl = (long long)g->nx * g->ny * g->nz;
   const long long ni = (long long)(g->p - 2) * (g->p - 2) * (g->p - 2), nb = 6LL * g->q * g->q;
-  double *T = nullptr, *dxi = nullptr, *dxf = nullptr;
+  double *T = nullptr, *dxi = nullptr, *dxf = nullptr, *dxc = nullptr;
   auto cleanup = [&]() {
     if (T) cudaFree(T);
     if (dxi) cudaFree(dxi);
     if (dxf) cudaFree(dxf);
+    if (dxc) cudaFree(dxc);
   };
   auto body = [&]() -> int {
     HPS_CUDA_TRY(cudaMalloc(&T, tl.total * sizeof(double)));
     if (xi) HPS_CUDA_TRY(cudaMalloc(&dxi, nl * ni * 3 * sizeof(double)));
     if (xf) HPS_CUDA_TRY(cudaMalloc(&dxf, nl * nb * 3 * sizeof(double)));
+    if (xc) HPS_CUDA_TRY(cudaMalloc(&dxc, nl * nb * 3 * sizeof(double)));
     HPS_CUDA_TRY(launch_tables(T, tl, 1.0 / g->nx, 1.0 / g->ny, 1.0 / g->nz, 0));
-    HPS_CUDA_TRY(launch_nodes(T, tl, g->nx, g->ny, g->nz, dxi, dxf, 0));
+    HPS_CUDA_TRY(launch_nodes(T, tl, g->nx, g->ny, g->nz, dxi, dxf, dxc, 0));
     if (xi) HPS_CUDA_TRY(cudaMemcpy(xi, dxi, nl * ni * 3 * sizeof(double), cudaMemcpyDeviceToHost));
     if (xf) HPS_CUDA_TRY(cudaMemcpy(xf, dxf, nl * nb * 3 * sizeof(double), cudaMemcpyDeviceToHost));
+    if (xc) HPS_CUDA_TRY(cudaMemcpy(xc, dxc, nl * nb * 3 * sizeof(double), cudaMemcpyDeviceToHost));
     return HPS_OK;
   };
   rc = body();
@@ -280,33 +290,33 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
     if (o.cluster == 2) {
       build_cluster_tables(h, 2);
       h->has_precond = true;
+      if ((r = classify_preconditioner(h, dc, st))) return r;
       const ClusterTables& ct = h->ct;
+      const size_t ke = std::max<long long>(1, ct.kc_elems), be = std::max<long long>(1, ct.b_elems);
       if (want64) {
-        if ((r = dalloc(h, (void**)&h->Kc64, std::max<long long>(1, ct.kc_elems) * sizeof(double2)))) return r;
-        if ((r = dalloc(h, (void**)&h->B64, std::max<long long>(1, ct.b_elems) * sizeof(double2)))) return r;
-        HPS_CUDA_TRY(cudaMemsetAsync(h->Kc64, 0, std::max<long long>(1, ct.kc_elems) * sizeof(double2), st));
-        HPS_CUDA_TRY(cudaMemsetAsync(h->B64, 0, std::max<long long>(1, ct.b_elems) * sizeof(double2), st));
+        if ((r = dalloc(h, (void**)&h->Kc64, ke * sizeof(double2)))) return r;
+        if ((r = dalloc(h, (void**)&h->B64, be * sizeof(double2)))) return r;
+        HPS_CUDA_TRY(cudaMemsetAsync(h->Kc64, 0, ke * sizeof(double2), st));
+        HPS_CUDA_TRY(cudaMemsetAsync(h->B64, 0, be * sizeof(double2), st));
       }
       const bool fp16 = want32 && (o.precond_fp16 || o.lean);
       if (want32) {
-        if (!o.lean &&
-            (r = dalloc(h, (void**)&h->Kc32, std::max<long long>(1, ct.kc_elems) * sizeof(float2))))
-          return r;
-        if ((r = dalloc(h, (void**)&h->B32, std::max<long long>(1, ct.b_elems) * sizeof(float2)))) return r;
-        if (h->Kc32) HPS_CUDA_TRY(cudaMemsetAsync(h->Kc32, 0, std::max<long long>(1, ct.kc_elems) * sizeof(float2), st));
-        HPS_CUDA_TRY(cudaMemsetAsync(h->B32, 0, std::max<long long>(1, ct.b_elems) * sizeof(float2), st));
+        if (!o.lean && (r = dalloc(h, (void**)&h->Kc32, ke * sizeof(float2)))) return r;
+        if ((r = dalloc(h, (void**)&h->B32, be * sizeof(float2)))) return r;
+        if (h->Kc32) HPS_CUDA_TRY(cudaMemsetAsync(h->Kc32, 0, ke * sizeof(float2), st));
+        HPS_CUDA_TRY(cudaMemsetAsync(h->B32, 0, be * sizeof(float2), st));
       }
       if (fp16) {
         const int q2 = h->q * h->q;
-        const size_t ke = std::max<long long>(1, ct.kc_elems), be = std::max<long long>(1, ct.b_elems);
         if ((r = dalloc(h, (void**)&h->Kc16, ke * sizeof(__half2)))) return r;
         if ((r = dalloc(h, (void**)&h->B16, be * sizeof(__half2)))) return r;
-        if ((r = dalloc(h, (void**)&h->Kc16s, std::max<size_t>(1, (size_t)ct.nslots * q2) * sizeof(float)))) return r;
-        if ((r = dalloc(h, (void**)&h->B16s, (size_t)h->nl * 6 * q2 * sizeof(float)))) return r;
+        const size_t kr = std::max<size_t>(1, (size_t)ct.kc_slot_begin[ct.nkc] * q2);
+        if ((r = dalloc(h, (void**)&h->Kc16s, kr * sizeof(float)))) return r;
+        if ((r = dalloc(h, (void**)&h->B16s, std::max<size_t>(1, (size_t)ct.nbc * 6 * q2) * sizeof(float)))) return r;
         HPS_CUDA_TRY(cudaMemsetAsync(h->Kc16, 0, ke * sizeof(__half2), st));
         HPS_CUDA_TRY(cudaMemsetAsync(h->B16, 0, be * sizeof(__half2), st));
       }
-      const size_t ts = std::max<size_t>(1, (size_t)ct.nslots * h->q * h->q) * o.max_rhs * sizeof(double2);
+      const size_t ts = (size_t)ct.tsize * o.max_rhs * sizeof(double2);
       if ((r = dalloc(h, &h->pc_scratch, ts))) return r;
       if ((r = build_preconditioner(h, dc, st))) return r;
       if (fp16 && (r = build_precond_fp16(h, st))) return r;
@@ -343,7 +353,7 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
   size_t bytes = h.tl.total * sizeof(double) + (o.lean ? 0 : rel * c16) + (want32 ? rel * c8 : 0) +
                  hel * (o.lean ? c8 : c16) + (size_t)h.nl * c16;
   const int q2 = h.q * h.q;
-  size_t nslots = 0;
+  size_t nslots = 0, tsize = 1;
   if (o.cluster == 2) {
     build_cluster_tables(&h, 2);
     const ClusterTables& ct = h.ct;
@@ -351,19 +361,23 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
     bytes += 2 * ct.slot_lf.size() * sizeof(int) + ct.cl_slot_begin.size() * sizeof(int) +
              ct.cl_kc_off.size() * sizeof(long long) + ct.lf_slot.size() * sizeof(int) + ct.int_mask.size() +
              ct.b_off.size() * sizeof(long long);
+    bytes += (size_t)h.nl * (2 * sizeof(int) + c16) + ct.kc_off.size() * sizeof(long long) +
+             (ct.kc_slot_begin.size() + ct.kslot_class.size() + ct.kc_members.size()) * sizeof(int);
+    for (const auto& v : ct.kitems) bytes += std::max<size_t>(1, v.size()) * sizeof(int4);
     if (want64) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c16;
     if (want32) bytes += (size_t)((o.lean ? 0 : ct.kc_elems) + ct.b_elems) * c8;
     if (want32 && (o.precond_fp16 || o.lean))
       bytes += (size_t)(ct.kc_elems + ct.b_elems) * sizeof(__half2) + nslots * q2 * sizeof(float) +
                (size_t)h.nl * 6 * q2 * sizeof(float);
-    bytes += std::max<size_t>(1, nslots * q2) * o.max_rhs * c16;
+    bytes += (size_t)ct.tsize * o.max_rhs * c16;
+    tsize = ct.tsize;
   }
   bytes += (size_t)h.nint * c16 + sizeof(int);  // medium C kept for recovery, error word
   // Krylov workspace of one solve (host inputs staged on the device)
   const int M1 = o.restart + 1;
   const size_t vb = (size_t)nrhs * h.nf * c16;
   const long long nblk = (h.nf + 1023) / 1024;
-  bytes += vb * (M1 + 5) + std::max<size_t>(1, nslots * q2) * nrhs * c16 + (size_t)nrhs * nblk * M1 * c16 +
+  bytes += vb * (M1 + 5) + tsize * nrhs * c16 + (size_t)nrhs * nblk * M1 * c16 +
            (size_t)o.max_rhs * (h.nint + h.nf) * c16 + (size_t)nrhs * (3 * M1 + 4 * o.restart + 8) * c16 +
            (size_t)nrhs * std::max<long long>(256, nblk) * sizeof(double);
   // transient setup workspace (largest phase) + medium staging
@@ -468,7 +482,7 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
     set_error("hps_gmres_solve: nrhs exceeds options.max_rhs");
     return HPS_EINVAL;
   }
-  if (form == HPS_FORM_MIXED && (!h->R32 || (h->has_precond && !no_pc && !h->Kc32))) {
+  if (form == HPS_FORM_MIXED && (!h->R32 || (h->has_precond && !no_pc && !h->Kc32 && !h->Kc16))) {
     set_error("hps_gmres_solve: mixed-form operators were not built");
     return HPS_EINVAL;
   }
@@ -517,13 +531,26 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
   return rc;
 }
 
-int hps_recover(hps_handle* h, const double* s, const double* f, int nrhs, double* u_out, void* stream) {
+int hps_recover(hps_handle* h, const double* s, const double* f, int nrhs, double* u_out, double* u_face_out,
+                void* stream) {
   if (!h || !f || !u_out || nrhs < 1 || nrhs > 1024) {
     set_error("hps_recover: bad arguments");
     return HPS_EINVAL;
   }
   HPS_CUDA_TRY(cudaSetDevice(h->dev));
-  return recover_interior(h, (const double2*)s, (const double2*)f, nrhs, (double2*)u_out, (cudaStream_t)stream);
+  return recover_interior(h, (const double2*)s, (const double2*)f, nrhs, (double2*)u_out, (double2*)u_face_out,
+                          (cudaStream_t)stream);
+}
+
+int hps_precond_info(const hps_handle* h, int* clusters, int* k_blocks, int* b_blocks) {
+  if (!h || !h->has_precond) {
+    set_error("hps_precond_info: no preconditioner");
+    return HPS_EINVAL;
+  }
+  if (clusters) *clusters = h->ct.ncl;
+  if (k_blocks) *k_blocks = h->ct.nkc;
+  if (b_blocks) *b_blocks = h->ct.nbc;
+  return HPS_OK;
 }
 
 long long hps_export(hps_handle* h, int what, int index, double* host_out) {

@@ -8,8 +8,10 @@
 //      stage B  z_ext = r_ext,  t = r_int - B r_ext   (B = internal rows of R~)
 //      stage K  z_int = K_c t                          (K_c = (I + D)^{-1})
 //
-// An item is (leaf, face) for apply/rhs/B (rows of that face's block) and a
-// cluster-internal slot for K.  The swap Pi is fused into the store: the rows
+// An item is (leaf, face) for apply/rhs (rows of that face's block), a leaf
+// for B, and for K one slot of a distinct K block against up to 8 clusters
+// sharing that block (their t vectors take the place of right-hand sides, so
+// a block shared by many clusters is read once per 8 of them).  The swap Pi is fused into the store: the rows
 // of leaf tau's face k produce the incoming data of the neighbour across k,
 // so every output slot has exactly one writer and no atomics are needed.
 // Faces on the boundary of the cube only copy (their rows of R are never
@@ -18,6 +20,7 @@
 // floats per lane per load), accumulates in the matrix's precision and
 // reduces with warp shuffles.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "hps_internal.h"
@@ -212,10 +215,11 @@ struct PrecBP {
   using Acc = typename MT<TM>::Acc;
   struct Args {
     const TM* B;
-    const float* bscale;  // FP16 blocks: row scales, index (leaf*6 + face)*q2 + j
+    const float* bscale;  // FP16 blocks: row scales, index (bcls[leaf]*6 + face)*q2 + j
+    const int* bcls;
     const long long* b_off;
     const uint8_t* int_mask;
-    const int* lf_slot;
+    const long long* lf_tpos;
     int nb, q2;
     GridDims g;
     const TIN* r;
@@ -259,8 +263,8 @@ struct PrecBP {
       const int face = nth_face(it.mask, row / A.q2, true), j = row % A.q2;
       const int nbr = A.g.neighbor(it.leaf, face);
       const long long aoff = (long long)nbr * A.nb + (long long)(face ^ 1) * A.q2;
-      const long long ooff = (long long)A.lf_slot[nbr * 6 + (face ^ 1)] * A.q2;
-      const Acc g = rscale(outs[idx], A.bscale, ((long long)it.leaf * 6 + face) * A.q2 + j);
+      const long long ooff = A.lf_tpos[nbr * 6 + (face ^ 1)];
+      const Acc g = rscale(outs[idx], A.bscale, ((long long)A.bcls[it.leaf] * 6 + face) * A.q2 + j);
       const Acc v = csub(cvt<Acc>(A.r[rhs * A.nf + aoff + j]), g);
       A.t[rhs * A.tstride + ooff + j] = cvt<TOUT>(v);
     }
@@ -278,45 +282,56 @@ struct PrecBP {
   }
 };
 
+// Stage K over distinct blocks: item = (block k, block slot s, first member,
+// member count) with the members the clusters sharing block k; "right-hand
+// side" rr of the item is member rr (one right-hand side per launch).
 template <class TM_, class TIN, class TOUT>
 struct PrecKP {
   using TM = TM_;
   using Acc = typename MT<TM>::Acc;
   struct Args {
     const TM* K;
-    const float* kscale;  // FP16 blocks: row scales, index slot*q2 + j
+    const float* kscale;  // FP16 blocks: row scales, index (kc_slot_begin[k] + s)*q2 + j
+    const int4* items;
     const long long* kc_off;
+    const int* kc_slot_begin;
+    const int* members;
     const int* cl_slot_begin;
-    const int* slot_cluster;
     const int* slot_lf;
+    const long long* cl_tpos;
     int nb, q2;
     const TIN* t;
     TOUT* z;
     long long nf, tstride;
-    int nrhs;
+    int nrhs;  // group width of the launch
     long long nitems;
   };
   __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
-    const int gs = (int)item;
-    const int c = A.slot_cluster[gs];
-    const int s0 = A.cl_slot_begin[c], ns = A.cl_slot_begin[c + 1] - s0;
+    const int4 e = A.items[item];
+    const int k = e.x, s = e.y;
+    const int s0 = A.kc_slot_begin[k], ns = A.kc_slot_begin[k + 1] - s0;
     it.ncols = ns * A.q2;
     it.ld = (int)rup4(it.ncols);
-    it.mat = A.K + A.kc_off[c] + (long long)(gs - s0) * A.q2 * it.ld;
+    it.mat = A.K + A.kc_off[k] + (long long)s * A.q2 * it.ld;
     it.nrows = A.q2;
-    it.xoff = (long long)s0 * A.q2;
-    const int lf = A.slot_lf[gs];
-    it.ooff = (long long)(lf / 6) * A.nb + (long long)(lf % 6) * A.q2;
-    it.aoff = (long long)gs * A.q2;
+    it.face = s;
+    it.xoff = e.z;  // first member
+    it.mask = e.w;  // members
+    it.aoff = (long long)(s0 + s) * A.q2;
     return true;
   }
-  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
-    return cvt<Acc>(A.t[rhs * A.tstride + it.xoff + c]);
+  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rr, int c) {
+    if (rr >= it.mask) return czero<Acc>();
+    const int cl = A.members[it.xoff + rr];
+    return cvt<Acc>(A.t[A.cl_tpos[cl] + c]);
   }
-  __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
-    for (int idx = tid; idx < nr * A.q2; idx += kThreads) {
-      const int rhs = idx / A.q2, j = idx % A.q2;
-      A.z[rhs * A.nf + it.ooff + j] = cvt<TOUT>(rscale(outs[idx], A.kscale, it.aoff + j));
+  __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int, int tid) {
+    for (int idx = tid; idx < it.mask * A.q2; idx += kThreads) {
+      const int rr = idx / A.q2, j = idx % A.q2;
+      const int cl = A.members[it.xoff + rr];
+      const int lf = A.slot_lf[A.cl_slot_begin[cl] + it.face];
+      const long long o = (long long)(lf / 6) * A.nb + (long long)(lf % 6) * A.q2 + j;
+      A.z[o] = cvt<TOUT>(rscale(outs[idx], A.kscale, it.aoff + j));
     }
   }
   __device__ static void copy(const Args&, const ItemInfo&, int, int) {}
@@ -470,17 +485,19 @@ cudaError_t apply_t(const hps_handle* h, const TM* R, const TIN* f, TOUT* y, con
 
 template <class TM, class TIN, class TOUT>
 cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* r, TOUT* z, TOUT* t, int nrhs,
-                      cudaStream_t st, const float* bscale = nullptr, const float* kscale = nullptr) {
+                      cudaStream_t st, const float* bscale = nullptr, const float* kscale = nullptr,
+                      bool use_tc = false) {
   const int q2 = h->q * h->q;
-  const long long tstride = (long long)h->ct.nslots * q2;
+  const long long tstride = h->ct.tsize;
   {
     using P = PrecBP<TM, TIN, TOUT>;
     typename P::Args A;
     A.B = B;
     A.bscale = bscale;
+    A.bcls = h->dct.leaf_bcls;
     A.b_off = h->dct.b_off;
     A.int_mask = h->dct.int_mask;
-    A.lf_slot = h->dct.lf_slot;
+    A.lf_tpos = h->dct.lf_tpos;
     A.nb = h->nb;
     A.q2 = q2;
     A.g = GridDims{h->nx, h->ny, h->nz};
@@ -506,23 +523,41 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     typename P::Args A;
     A.K = K;
     A.kscale = kscale;
-    A.kc_off = h->dct.cl_kc_off;
+    A.kc_off = h->dct.kc_off;
+    A.kc_slot_begin = h->dct.kc_slot_begin;
+    A.members = h->dct.kc_members;
     A.cl_slot_begin = h->dct.cl_slot_begin;
-    A.slot_cluster = h->dct.slot_cluster;
     A.slot_lf = h->dct.slot_lf;
+    A.cl_tpos = h->dct.cl_tpos;
     A.nb = h->nb;
     A.q2 = q2;
-    A.t = t;
-    A.z = z;
     A.nf = h->nf;
     A.tstride = tstride;
-    A.nrhs = nrhs;
-    A.nitems = h->ct.nslots;
+    const int xcap = xcap_of(h);
+    long long* counter = &h->prof.launches;
     cudaEvent_t ev = h->prof.begin(st);
-    cudaError_t e = launch_groups<P>(h, A, nrhs, xcap_of(h), q2, st, [&](typename P::Args& X, int r0) {
-      X.t += (long long)r0 * tstride;
-      X.z += (long long)r0 * h->nf;
-    });
+    cudaError_t e = cudaSuccess;
+    for (int rhs = 0; rhs < nrhs && e == cudaSuccess; ++rhs) {
+      A.t = t + (long long)rhs * tstride;
+      A.z = z + (long long)rhs * h->nf;
+      if (use_tc) {
+        if constexpr (std::is_same<TOUT, float2>::value)
+          e = launch_precond_tc(h, (const float2*)A.t, (float2*)A.z, h->tc_error, st);
+        else
+          e = cudaErrorInvalidValue;
+      }
+      for (int g = 0; g < 4 && e == cudaSuccess; ++g) {
+        const long long n = use_tc ? h->ct.kitems_ntc[g] : (long long)h->ct.kitems[g].size();
+        if (n == 0) continue;
+        A.items = h->dct.kitems[g];
+        A.nitems = n;
+        A.nrhs = 1 << g;
+        if (g == 0) e = launch_one<P, 1, 4>(A, xcap, q2, h->nsm, st, counter);
+        else if (g == 1) e = launch_one<P, 2, 4>(A, xcap, q2, h->nsm, st, counter);
+        else if (g == 2) e = launch_one<P, 4, 2>(A, xcap, q2, h->nsm, st, counter);
+        else e = launch_one<P, 8, 2>(A, xcap, q2, h->nsm, st, counter);
+      }
+    }
     h->prof.end(HPS_PHASE_PRECOND_K, ev, st);
     return e;
   }
@@ -605,19 +640,26 @@ cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, con
     return cudaErrorInvalidValue;
   }
   if (tout != VType::C64) return cudaErrorInvalidValue;
+  // shared K blocks with many member clusters: complex-FP32 blocks on the tensor cores
+  const bool tc = h->opt.tc_apply && h->Kc32 && h->tc_error && !h->ct.kc_tc.empty();
   if (fp16_blocks) {
     if (!h->Kc16 || !h->B16) return cudaErrorInvalidValue;
     if (tin == VType::C64)
-      return precond_t(h, h->B16, h->Kc16, (const float2*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s);
+      return precond_t(h, h->B16, h->Kc16, (const float2*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s,
+                       tc);
     if (tin == VType::DF)
-      return precond_t(h, h->B16, h->Kc16, (const float4*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s);
-    return precond_t(h, h->B16, h->Kc16, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s);
+      return precond_t(h, h->B16, h->Kc16, (const float4*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s,
+                       tc);
+    return precond_t(h, h->B16, h->Kc16, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st, h->B16s, h->Kc16s,
+                     tc);
   }
   if (tin == VType::C64)
-    return precond_t(h, h->B32, h->Kc32, (const float2*)r, (float2*)z, (float2*)scratch, nrhs, st);
+    return precond_t(h, h->B32, h->Kc32, (const float2*)r, (float2*)z, (float2*)scratch, nrhs, st, nullptr, nullptr,
+                     tc);
   if (tin == VType::DF)
-    return precond_t(h, h->B32, h->Kc32, (const float4*)r, (float2*)z, (float2*)scratch, nrhs, st);
-  return precond_t(h, h->B32, h->Kc32, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st);
+    return precond_t(h, h->B32, h->Kc32, (const float4*)r, (float2*)z, (float2*)scratch, nrhs, st, nullptr, nullptr,
+                     tc);
+  return precond_t(h, h->B32, h->Kc32, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st, nullptr, nullptr, tc);
 }
 
 }  // namespace hps

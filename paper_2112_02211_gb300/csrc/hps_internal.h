@@ -53,18 +53,53 @@ struct TableLayout {
 
 // Cluster (block-Jacobi) bookkeeping, built on the host from integer grid
 // arithmetic and uploaded once.
+//
+// Distinct blocks: clusters whose leaves carry the same (binned) homogenized
+// constants lambda^tau in the same arrangement share one K block, and leaves
+// with the same constant and the same internal-face mask share one B block
+// (reuse of the local solver for leaves with nearly the same medium, Sec. 4.1
+// remark).  Without binning every cluster and leaf owns its block unless two
+// constants are bitwise equal.
 struct ClusterTables {
   int ncl = 0;                       // clusters
   int nslots = 0;                    // internal face slots over all clusters
   std::vector<int> cl_leaf_begin;    // [ncl+1] into cl_leaves
   std::vector<int> cl_leaves;        // leaves of each cluster, lexicographic
   std::vector<int> cl_slot_begin;    // [ncl+1] first global slot of each cluster
-  std::vector<long long> cl_kc_off;  // [ncl] element offset of K_c (ld = kc_ld(c))
+  std::vector<long long> cl_kc_off;  // [ncl] element offset of the cluster's K block (ld = rup4(nint))
   std::vector<int> slot_lf;          // [nslots] leaf*6+face of each slot
   std::vector<int> slot_cluster;     // [nslots]
   std::vector<int> lf_slot;          // [nleaves*6] slot of (leaf, face) or -1 if external
   std::vector<uint8_t> int_mask;     // [nleaves] bit f: face f is internal to the leaf's cluster
-  std::vector<long long> b_off;      // [nleaves] element offset of B^leaf
+  std::vector<long long> b_off;      // [nleaves] element offset of the leaf's B block
+  // distinct K blocks
+  int nkc = 0;
+  std::vector<int> cl_class;         // [ncl] K block of each cluster
+  std::vector<int> kc_rep;           // [nkc] first cluster using the block
+  std::vector<int> kc_slot_begin;    // [nkc+1] block slots; FP16 scale row = (kc_slot_begin[k] + s) q^2 + j
+  std::vector<long long> kc_off;     // [nkc] element offset of block k
+  std::vector<int> kc_members;       // clusters grouped by block, ascending within a block
+  std::vector<int> kc_mem_begin;     // [nkc+1] into kc_members
+  std::vector<int> kslot_class;      // [kc_slot_begin[nkc]] block of each block slot
+  // distinct B blocks
+  int nbc = 0;
+  std::vector<int> leaf_bcls;        // [nleaves] B block of each leaf; FP16 scale row = (bcls*6 + face) q^2 + j
+  std::vector<int> bc_rep;           // [nbc] first leaf using the block
+  // stage-K work items (block, block slot, first member, member count) for
+  // member groups of width 1, 2, 4 and 8, and the blocks whose members are
+  // many enough for the tensor-core path (tc_precond.cu), which then skip the
+  // items above
+  std::vector<int4> kitems[4];
+  long long kitems_ntc[4] = {0, 0, 0, 0};
+  std::vector<int> kc_tc;
+  // stage-K input t: the members of a block are consecutive and each block
+  // starts on a 16-element boundary, so a block's t vectors form one strided
+  // matrix; cl_tpos[c] is cluster c's offset, lf_tpos[leaf*6+face] the offset
+  // of an internal face's q^2 values (-1 on external faces), tsize the
+  // elements per right-hand side
+  std::vector<long long> cl_tpos;
+  std::vector<long long> lf_tpos;
+  long long tsize = 0;
   long long kc_elems = 0, b_elems = 0;
 };
 
@@ -76,6 +111,15 @@ struct DeviceClusterTables {
   int* lf_slot = nullptr;
   uint8_t* int_mask = nullptr;
   long long* b_off = nullptr;
+  int* leaf_bcls = nullptr;
+  int* bc_rep = nullptr;
+  long long* kc_off = nullptr;
+  int* kc_slot_begin = nullptr;
+  int* kslot_class = nullptr;
+  int* kc_members = nullptr;
+  int4* kitems[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long* cl_tpos = nullptr;
+  long long* lf_tpos = nullptr;
 };
 
 // Per-phase CUDA-event timing and a launch counter (see hps_profile).
@@ -187,7 +231,8 @@ struct hps_handle {
   float2* R32 = nullptr;   // nl x nb x ldR
   double2* H64 = nullptr;  // nl x nb x ldH
   float2* H32 = nullptr;   // nl x nb x ldH (lean mode instead of H64)
-  double2* lambda = nullptr;  // nl
+  double2* lambda = nullptr;    // nl: homogenized constants lambda^tau
+  double2* lambda_q = nullptr;  // nl: lambda^tau after binning (opt.lambda_bin), used by the preconditioner
   double2* cdiag = nullptr;   // nl x ni: C = kappa^2 (1 - b) at interior nodes (kept for recovery)
 
   // preconditioner
@@ -198,9 +243,9 @@ struct hps_handle {
   float2* Kc32 = nullptr;
   double2* B64 = nullptr;
   float2* B32 = nullptr;
-  __half2* Kc16 = nullptr;  // FP16 copies, row r scaled by 1/Kc16s[r] (global row = slot*q^2 + j)
+  __half2* Kc16 = nullptr;  // FP16 copies, row r of block slot bs scaled by 1/Kc16s[bs*q^2 + r]
   float* Kc16s = nullptr;
-  __half2* B16 = nullptr;   // FP16 copies of B, rows scaled by 1/B16s[(leaf*6+face)*q^2 + j]
+  __half2* B16 = nullptr;   // FP16 copies of B, rows scaled by 1/B16s[(bcls*6+face)*q^2 + j]
   float* B16s = nullptr;
   void* pc_scratch = nullptr;  // nslots*q^2*max_rhs complex double (precond t buffer)
 
@@ -216,16 +261,27 @@ namespace hps {
 cudaError_t launch_tables(double* tables, const TableLayout& tl, double hx, double hy, double hz,
                           cudaStream_t st);
 cudaError_t launch_nodes(const double* tables, const TableLayout& tl, int nx, int ny, int nz,
-                         double* interior_xyz_dev, double* face_xyz_dev, cudaStream_t st);
+                         double* interior_xyz_dev, double* face_xyz_dev, double* cheb_face_xyz_dev,
+                         cudaStream_t st);
 // Builds R (and H) for all leaves; see setup.cu.
 int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st);
+// lambda^tau of every leaf, its binning and the distinct preconditioner blocks
+// (sizes in h->ct); uploads the cluster tables.  Before the block storage is
+// allocated.
+int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st);
 int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st);
 int build_precond_fp16(hps_handle* h, cudaStream_t st);
-int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, cudaStream_t st);
+int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, double2* uf,
+                     cudaStream_t st);
 size_t workspace_cap(const hps_handle* h);
 size_t exact_maps_workspace(const hps_handle* h, size_t budget, int* nbatch_out);
 size_t precond_workspace(const hps_handle* h, size_t budget, int* cb_out);
 void build_cluster_tables(hps_handle* h, int width);
+// Distinct preconditioner blocks from binned lambda values (nullptr: one block
+// per cluster and per leaf).
+void assign_blocks(hps_handle* h, const std::vector<double2>* lamq);
+// Shared K blocks with at least this many member clusters run on the tensor cores.
+constexpr int kTcMinMembers = 16;
 
 // ---- apply.cu ----
 // C128 complex double, C64 complex float, DF complex double-float (float4: re.h, im.h, re.l, im.l)
@@ -242,6 +298,10 @@ cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, con
 // float or double-float; nrhs a multiple of 64.
 cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool out_df, int nrhs, int* d_error,
                             cudaStream_t st);
+// Stage K of the preconditioner for the shared K blocks listed in ct.kc_tc, on
+// the tensor cores (tc_precond.cu): z_int = K_c t for every member cluster of
+// those blocks; one right-hand side; t in the class-ordered layout.
+cudaError_t launch_precond_tc(const hps_handle* h, const float2* t, float2* z, int* d_error, cudaStream_t st);
 // Timed wrappers (phase intervals recorded when profiling is on).
 cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType tin, const void* f, VType tout,
                         void* y, const double2* bvec, int nrhs, bool residual, cudaStream_t st);

@@ -529,11 +529,6 @@ __global__ void xpy_kernel(double2* x, const T* z, long long n) {
     x[i] = cadd(x[i], cvt<double2>(z[i]));
 }
 
-__global__ void cast_vec_kernel(const double2* in, float2* out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = cvt<float2>(in[i]);
-}
-
 // norms[rhs] = ||x_rhs||_2 from block partials
 __global__ void norm_partial_kernel(const double2* x, long long nf, int nblk, double* part) {
   const int rhs = blockIdx.y, blk = blockIdx.x;
@@ -600,7 +595,7 @@ int krylov_alloc(hps_handle* h, int nrhs) {
   if ((rc = alloc((void**)&k.b, vb))) return rc;
   if ((rc = alloc((void**)&k.u, vb))) return rc;
   if ((rc = alloc(&k.z, vb))) return rc;
-  const size_t ts = std::max<size_t>(1, (size_t)h->ct.nslots * h->q * h->q) * nrhs * sizeof(double2);
+  const size_t ts = (size_t)std::max<long long>(1, h->ct.tsize) * nrhs * sizeof(double2);
   if ((rc = alloc(&k.zt, ts))) return rc;
   if ((rc = alloc((void**)&k.part, (size_t)nrhs * k.nblk * M1 * sizeof(double2)))) return rc;
   if ((rc = alloc((void**)&k.hcol, (size_t)nrhs * (M1 + 1) * sizeof(double2)))) return rc;

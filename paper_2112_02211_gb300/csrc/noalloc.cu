@@ -19,7 +19,8 @@ namespace hps {
 namespace {
 
 // The scratch holds the cluster-internal right-hand sides t (stage B output,
-// stage K input): nslots * q^2 * nrhs complex values of the call's type.
+// stage K input): tsize * nrhs complex values of the call's type (tsize: the
+// internal-face values of all clusters, blocks padded to 16 values).
 // Every device that loads the library reserves these bytes until the process exits.
 constexpr size_t kNoAllocScratchBytes = HPS_PRECOND_NOALLOC_MAX_BYTES;
 
@@ -70,7 +71,7 @@ int hps_precond_noalloc(hps_handle* h, int dtype, const void* r, void* z, int nr
     return HPS_EINVAL;
   }
   const size_t es = (dtype == HPS_C128) ? sizeof(double2) : sizeof(float2);
-  const size_t need = (size_t)h->ct.nslots * h->q * h->q * (size_t)nrhs * es;
+  const size_t need = (size_t)h->ct.tsize * (size_t)nrhs * es;
   if (need > kNoAllocScratchBytes) {
     set_error("hps_precond_noalloc: needs " + std::to_string(need) + " bytes of scratch, more than the " +
               std::to_string(kNoAllocScratchBytes) + "-byte static buffer; use hps_precond or fewer right-hand sides");

@@ -18,9 +18,12 @@
 // here by the same elimination kernel) and the blocks B^beta of R~ (internal
 // rows, external columns of each leaf).
 #include <algorithm>
-#include <type_traits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <tuple>
+#include <type_traits>
 
 #include "common.cuh"
 #include "hps_internal.h"
@@ -143,7 +146,7 @@ __global__ void tables_kernel(double* T, TableLayout tl, double hx, double hy, d
 // Node coordinates.
 // ---------------------------------------------------------------------------
 __global__ void nodes_kernel(const double* T, TableLayout tl, int nx, int ny, int nz, double* xi,
-                             double* xf) {
+                             double* xf, double* xc) {
   const int p = tl.p, q = tl.q, n1 = p - 2;
   const long long nl = (long long)nx * ny * nz;
   const long long ni = (long long)n1 * n1 * n1, nb = 6LL * q * q;
@@ -173,6 +176,16 @@ __global__ void nodes_kernel(const double* T, TableLayout tl, int nx, int ny, in
       o[axis] = c[axis] + ((face & 1) ? h[axis] : 0.0);
       o[a0] = c[a0] + 0.5 * h[a0] * (xg[j1] + 1.0);
       o[a1] = c[a1] + 0.5 * h[a1] * (xg[j2] + 1.0);
+    }
+    if (xc && r < nb) {  // Chebyshev face nodes (q == n1): first in-face axis fastest
+      int face = (int)(r / (q * q)), jj = (int)(r % (q * q));
+      int a = jj % q + 1, bb = jj / q + 1;
+      int axis = face >> 1;
+      int a0 = (axis == 0) ? 1 : 0, a1 = (axis == 2) ? 1 : 2;
+      double* o = xc + 3 * (leaf * nb + r);
+      o[axis] = c[axis] + ((face & 1) ? h[axis] : 0.0);
+      o[a0] = c[a0] + 0.5 * h[a0] * (x[a] + 1.0);
+      o[a1] = c[a1] + 0.5 * h[a1] * (x[bb] + 1.0);
     }
   }
 }
@@ -573,12 +586,16 @@ __global__ void recover_rhs_kernel(double2* W, long long wstride, int ld, int le
 }
 
 __global__ void recover_extract_kernel(const double2* W, long long wstride, int ld, int n, int ni, int leaf0,
-                                       int nbatch, int nrhs, long long nint, double2* u) {
+                                       int nbatch, int nrhs, long long nint, double2* u, long long nfc,
+                                       double2* uf) {
   const int b = blockIdx.y;
   if (b >= nbatch) return;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ni * nrhs; t += gridDim.x * blockDim.x) {
-    const int r = t % ni, k = t / ni;
-    u[k * nint + (long long)(leaf0 + b) * ni + r] = W[(long long)b * wstride + (long long)r * ld + n + k];
+  const int nb = n - ni;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * nrhs; t += gridDim.x * blockDim.x) {
+    const int r = t % n, k = t / n;
+    const double2 v = W[(long long)b * wstride + (long long)r * ld + n + k];
+    if (r < ni) u[k * nint + (long long)(leaf0 + b) * ni + r] = v;
+    else if (uf) uf[k * nfc + (long long)(leaf0 + b) * nb + (r - ni)] = v;
   }
 }
 
@@ -595,7 +612,7 @@ __device__ __forceinline__ void quantize_row(const float2* src, __half2* dst, in
   if (lane == 0) *scale = s;
 }
 
-// rows of every K_c; global row gr = slot * q^2 + j
+// rows of every distinct K block; row gr = block slot * q^2 + j
 __global__ void quantize_kc_kernel(const float2* K32, __half2* K16, float* kscale, const int* slot_cluster,
                                    const int* cl_slot_begin, const long long* kc_off, int q2, long long nrows) {
   const int lane = threadIdx.x & 31;
@@ -627,13 +644,13 @@ __global__ void quantize_kc_ws_kernel(const float2* W, long long wstride, int ld
                  kscale + (long long)s0 * q2 + r, lane);
 }
 
-// rows of every B^leaf; row index (leaf*6 + face)*q^2 + j for internal faces
-__global__ void quantize_b_kernel(const float2* B32, __half2* B16, float* bscale, const uint8_t* int_mask,
-                                  const long long* b_off, int q2, long long nrows) {
+// rows of every distinct B block; row index (block*6 + face)*q^2 + j for internal faces
+__global__ void quantize_b_kernel(const float2* B32, __half2* B16, float* bscale, const int* bc_rep,
+                                  const uint8_t* int_mask, const long long* b_off, int q2, long long nrows) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long gr = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); gr < nrows; gr += warps) {
-    const int leaf = (int)(gr / (6 * q2));
+    const int leaf = bc_rep[gr / (6 * q2)];
     const int face = (int)((gr / q2) % 6);
     const int j = (int)(gr % q2);
     const unsigned mask = int_mask[leaf];
@@ -649,16 +666,20 @@ __global__ void quantize_b_kernel(const float2* B32, __half2* B16, float* bscale
 
 // ---------------------------------------------------------------------------
 int build_precond_fp16(hps_handle* h, cudaStream_t st) {
+  const ClusterTables& ct = h->ct;
   const int q2 = h->q * h->q;
-  const long long krows = (long long)h->ct.nslots * q2;
-  const long long brows = (long long)h->nl * 6 * q2;
+  const long long krows = (long long)ct.kc_slot_begin[ct.nkc] * q2;
+  const long long brows = (long long)ct.nbc * 6 * q2;
   if (krows > 0 && h->Kc32) {  // lean mode quantized K_c during the build
-    quantize_kc_kernel<<<h->nsm * 8, 256, 0, st>>>(h->Kc32, h->Kc16, h->Kc16s, h->dct.slot_cluster,
-                                                    h->dct.cl_slot_begin, h->dct.cl_kc_off, q2, krows);
+    quantize_kc_kernel<<<h->nsm * 8, 256, 0, st>>>(h->Kc32, h->Kc16, h->Kc16s, h->dct.kslot_class,
+                                                    h->dct.kc_slot_begin, h->dct.kc_off, q2, krows);
     HPS_CUDA_TRY(cudaGetLastError());
   }
-  quantize_b_kernel<<<h->nsm * 8, 256, 0, st>>>(h->B32, h->B16, h->B16s, h->dct.int_mask, h->dct.b_off, q2, brows);
-  HPS_CUDA_TRY(cudaGetLastError());
+  if (brows > 0) {
+    quantize_b_kernel<<<h->nsm * 8, 256, 0, st>>>(h->B32, h->B16, h->B16s, h->dct.bc_rep, h->dct.int_mask,
+                                                   h->dct.b_off, q2, brows);
+    HPS_CUDA_TRY(cudaGetLastError());
+  }
   HPS_CUDA_TRY(cudaStreamSynchronize(st));
   return HPS_OK;
 }
@@ -675,8 +696,8 @@ cudaError_t launch_cdiag(const double2* b, double kappa, long long count, double
 }
 
 cudaError_t launch_nodes(const double* tables, const TableLayout& tl, int nx, int ny, int nz,
-                         double* xi, double* xf, cudaStream_t st) {
-  nodes_kernel<<<1024, 256, 0, st>>>(tables, tl, nx, ny, nz, xi, xf);
+                         double* xi, double* xf, double* xc, cudaStream_t st) {
+  nodes_kernel<<<1024, 256, 0, st>>>(tables, tl, nx, ny, nz, xi, xf, xc);
   return cudaGetLastError();
 }
 
@@ -748,7 +769,8 @@ size_t precond_workspace(const hps_handle* h, size_t budget, int* cb_out) {
   const ClusterTables& ct = h->ct;
   const int q2 = h->q * h->q;
   int max_int = 0, max_leaves = 0;
-  for (int c = 0; c < ct.ncl; ++c) {
+  for (int k = 0; k < ct.nkc; ++k) {
+    const int c = ct.kc_rep[k];
     max_int = std::max(max_int, (ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2);
     max_leaves = std::max(max_leaves, ct.cl_leaf_begin[c + 1] - ct.cl_leaf_begin[c]);
   }
@@ -757,7 +779,7 @@ size_t precond_workspace(const hps_handle* h, size_t budget, int* cb_out) {
   const long long wc_stride = (long long)std::max(1, max_int) * ldw;
   const size_t per_cluster =
       ((size_t)wl_stride * max_leaves + (size_t)h->nb * h->ldR * max_leaves + (size_t)wc_stride) * sizeof(double2);
-  int cb = (int)std::min<size_t>((size_t)std::max(1, ct.ncl), std::max<size_t>(1, budget / per_cluster));
+  int cb = (int)std::min<size_t>((size_t)std::max(1, ct.nkc), std::max<size_t>(1, budget / per_cluster));
   cb = std::min(cb, std::max(1, 2 * h->nsm));
   if (cb_out) *cb_out = cb;
   return per_cluster * cb;
@@ -765,7 +787,8 @@ size_t precond_workspace(const hps_handle* h, size_t budget, int* cb_out) {
 
 // Interior values of the leaf solutions u^tau = A^{tau,-1} [s^tau; P^{-1} f^tau]
 // (eq. (leaf)), by FP64 elimination of each leaf system with nrhs extra columns.
-int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, cudaStream_t st) {
+int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, double2* uf,
+                     cudaStream_t st) {
   const int n = h->n, ni = h->ni;
   const int ncols = n + nrhs, ld = ncols;
   const long long wstride = (long long)n * ld;
@@ -790,7 +813,8 @@ int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs
                                                          h->nint, h->nf);
       HPS_CUDA_TRY(cudaGetLastError());
       HPS_CUDA_TRY(run_gj(W, wstride, ld, n, ncols, 0, nbt, d_status, st));
-      recover_extract_kernel<<<dim3(32, nbt), 128, 0, st>>>(W, wstride, ld, n, ni, l0, nbt, nrhs, h->nint, u);
+      recover_extract_kernel<<<dim3(32, nbt), 128, 0, st>>>(W, wstride, ld, n, ni, l0, nbt, nrhs, h->nint, u,
+                                                             (long long)h->nl * h->nb, uf);
       HPS_CUDA_TRY(cudaGetLastError());
       return HPS_OK;
     };
@@ -869,7 +893,6 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
 void build_cluster_tables(hps_handle* h, int width) {
   ClusterTables& ct = h->ct;
   ct = ClusterTables();
-  const int q2 = h->q * h->q;
   ct.lf_slot.assign((size_t)h->nl * 6, -1);
   ct.int_mask.assign(h->nl, 0);
   ct.b_off.assign(h->nl, 0);
@@ -903,36 +926,184 @@ void build_cluster_tables(hps_handle* h, int width) {
         ct.cl_leaf_begin.push_back((int)ct.cl_leaves.size());
         ct.cl_slot_begin.push_back(ct.nslots);
       }
-  ct.cl_kc_off.resize(ct.ncl);
-  long long off = 0;
-  for (int c = 0; c < ct.ncl; ++c) {
-    const long long nint = (long long)(ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2;
-    ct.cl_kc_off[c] = off;
-    off += nint * round_up(nint, 4);
-  }
-  ct.kc_elems = off;
-  off = 0;
+  assign_blocks(h, nullptr);
+}
+
+// Distinct preconditioner blocks.  With lamq == nullptr every cluster and leaf
+// owns its block (the sizes hps_setup_bytes reserves); otherwise leaves are
+// keyed by (binned lambda, internal-face mask) and clusters by the sequence of
+// their leaves' keys, which fixes the cluster's shape and its J_c exactly.
+void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
+  ClusterTables& ct = h->ct;
+  const int q2 = h->q * h->q;
+  auto bits = [](double v) {
+    v += 0.0;  // -0 and +0 are one constant
+    uint64_t u;
+    std::memcpy(&u, &v, sizeof(u));
+    return u;
+  };
+  // B blocks
+  ct.leaf_bcls.assign(h->nl, 0);
+  ct.bc_rep.clear();
+  std::map<std::tuple<uint64_t, uint64_t, int>, int> bkeys;
   for (int leaf = 0; leaf < h->nl; ++leaf) {
-    const int ni_ = __builtin_popcount(ct.int_mask[leaf]);
-    ct.b_off[leaf] = off;
+    int cls;
+    if (!lamq) {
+      cls = (int)ct.bc_rep.size();
+      ct.bc_rep.push_back(leaf);
+    } else {
+      const double2 l = (*lamq)[leaf];
+      auto key = std::make_tuple(bits(l.x), bits(l.y), (int)ct.int_mask[leaf]);
+      auto it = bkeys.find(key);
+      if (it == bkeys.end()) {
+        cls = (int)ct.bc_rep.size();
+        bkeys.emplace(key, cls);
+        ct.bc_rep.push_back(leaf);
+      } else {
+        cls = it->second;
+      }
+    }
+    ct.leaf_bcls[leaf] = cls;
+  }
+  ct.nbc = (int)ct.bc_rep.size();
+  std::vector<long long> bc_off(ct.nbc);
+  long long off = 0;
+  for (int k = 0; k < ct.nbc; ++k) {
+    const int ni_ = __builtin_popcount(ct.int_mask[ct.bc_rep[k]]);
+    bc_off[k] = off;
     off += (long long)ni_ * q2 * round_up((long long)(6 - ni_) * q2, 4);
   }
   ct.b_elems = off;
+  ct.b_off.assign(h->nl, 0);
+  for (int leaf = 0; leaf < h->nl; ++leaf) ct.b_off[leaf] = bc_off[ct.leaf_bcls[leaf]];
+  // K blocks
+  ct.cl_class.assign(ct.ncl, 0);
+  ct.kc_rep.clear();
+  std::map<std::vector<uint64_t>, int> kkeys;
+  for (int c = 0; c < ct.ncl; ++c) {
+    int cls;
+    if (!lamq) {
+      cls = (int)ct.kc_rep.size();
+      ct.kc_rep.push_back(c);
+    } else {
+      std::vector<uint64_t> key;
+      for (int l = ct.cl_leaf_begin[c]; l < ct.cl_leaf_begin[c + 1]; ++l) {
+        const int leaf = ct.cl_leaves[l];
+        const double2 v = (*lamq)[leaf];
+        key.push_back(bits(v.x));
+        key.push_back(bits(v.y));
+        key.push_back(ct.int_mask[leaf]);
+      }
+      auto it = kkeys.find(key);
+      if (it == kkeys.end()) {
+        cls = (int)ct.kc_rep.size();
+        kkeys.emplace(std::move(key), cls);
+        ct.kc_rep.push_back(c);
+      } else {
+        cls = it->second;
+      }
+    }
+    ct.cl_class[c] = cls;
+  }
+  ct.nkc = (int)ct.kc_rep.size();
+  ct.kc_slot_begin.assign(ct.nkc + 1, 0);
+  ct.kc_off.assign(ct.nkc, 0);
+  off = 0;
+  for (int k = 0; k < ct.nkc; ++k) {
+    const int c = ct.kc_rep[k];
+    const int ns = ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c];
+    const long long nint = (long long)ns * q2;
+    ct.kc_slot_begin[k + 1] = ct.kc_slot_begin[k] + ns;
+    ct.kc_off[k] = off;
+    off += nint * round_up(nint, 4);
+  }
+  ct.kc_elems = off;
+  ct.cl_kc_off.assign(ct.ncl, 0);
+  for (int c = 0; c < ct.ncl; ++c) ct.cl_kc_off[c] = ct.kc_off[ct.cl_class[c]];
+  ct.kslot_class.assign(ct.kc_slot_begin[ct.nkc], 0);
+  for (int k = 0; k < ct.nkc; ++k)
+    for (int s = ct.kc_slot_begin[k]; s < ct.kc_slot_begin[k + 1]; ++s) ct.kslot_class[s] = k;
+  // members of each block and the stage-K work items
+  ct.kc_mem_begin.assign(ct.nkc + 1, 0);
+  for (int c = 0; c < ct.ncl; ++c) ++ct.kc_mem_begin[ct.cl_class[c] + 1];
+  for (int k = 0; k < ct.nkc; ++k) ct.kc_mem_begin[k + 1] += ct.kc_mem_begin[k];
+  ct.kc_members.assign(ct.ncl, 0);
+  {
+    std::vector<int> fill(ct.kc_mem_begin.begin(), ct.kc_mem_begin.end() - 1);
+    for (int c = 0; c < ct.ncl; ++c) ct.kc_members[fill[ct.cl_class[c]]++] = c;
+  }
+  // widest member group whose staged vectors (complex double in the FP64 form)
+  // fit in shared memory: W * (xcap + q^2) * 16 bytes
+  int xcap = std::max(h->nb, h->ni);
+  for (int c = 0; c < ct.ncl; ++c) xcap = std::max(xcap, (ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2);
+  xcap = (int)round_up(xcap, 64);
+  int wmax = 8;
+  while (wmax > 1 && (size_t)wmax * (xcap + q2) * 16 > (size_t)220 * 1024) wmax >>= 1;
+  // class-ordered stage-K input layout
+  ct.cl_tpos.assign(ct.ncl, 0);
+  ct.lf_tpos.assign((size_t)h->nl * 6, -1);
+  {
+    long long pos = 0;
+    for (int k = 0; k < ct.nkc; ++k) {
+      pos = round_up(pos, 16);
+      for (int m = ct.kc_mem_begin[k]; m < ct.kc_mem_begin[k + 1]; ++m) {
+        const int c = ct.kc_members[m];
+        ct.cl_tpos[c] = pos;
+        for (int sl = ct.cl_slot_begin[c]; sl < ct.cl_slot_begin[c + 1]; ++sl)
+          ct.lf_tpos[ct.slot_lf[sl]] = pos + (long long)(sl - ct.cl_slot_begin[c]) * q2;
+        pos += (long long)(ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2;
+      }
+    }
+    ct.tsize = round_up(std::max<long long>(pos, 1), 16);
+  }
+  // blocks for the tensor-core path: many members, an even row length (16-byte
+  // aligned member rows of complex floats)
+  ct.kc_tc.clear();
+  for (int k = 0; k < ct.nkc; ++k) {
+    const int ns = ct.kc_slot_begin[k + 1] - ct.kc_slot_begin[k];
+    const int nmem = ct.kc_mem_begin[k + 1] - ct.kc_mem_begin[k];
+    if (lamq && ns > 0 && nmem >= kTcMinMembers && ((long long)ns * q2) % 2 == 0) ct.kc_tc.push_back(k);
+  }
+  // items of the tensor-core blocks go last in every bucket, so that the first
+  // kitems_ntc[g] items are the rest
+  for (auto& v : ct.kitems) v.clear();
+  std::vector<char> is_tc(ct.nkc, 0);
+  for (int k : ct.kc_tc) is_tc[k] = 1;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int k = 0; k < ct.nkc; ++k) {
+      const int ns = ct.kc_slot_begin[k + 1] - ct.kc_slot_begin[k];
+      if (ns == 0 || is_tc[k] != pass) continue;
+      int pos = ct.kc_mem_begin[k];
+      const int end = ct.kc_mem_begin[k + 1];
+      while (pos < end) {
+        const int cnt = std::min(end - pos, wmax);
+        int bucket = 0;
+        while ((1 << bucket) < cnt) ++bucket;
+        for (int sl = 0; sl < ns; ++sl) ct.kitems[bucket].push_back(make_int4(k, sl, pos, cnt));
+        pos += cnt;
+      }
+    }
+    if (pass == 0)
+      for (int g = 0; g < 4; ++g) ct.kitems_ntc[g] = (long long)ct.kitems[g].size();
+  }
 }
 
-// The cluster blocks built with elimination in T: complex double when the FP64
-// form is kept, complex float otherwise (the FP32 elimination gives the
-// boundary block of the inverse to ~2e-7, far below what a preconditioner
-// needs, at the FP32 rate).
+// The distinct cluster blocks, built with elimination in T: complex double
+// when the FP64 form is kept, complex float otherwise (the FP32 elimination
+// gives the boundary block of the inverse to ~2e-7, far below what a
+// preconditioner needs, at the FP32 rate).  One representative cluster per
+// block is built; its leaves' B blocks are the distinct B blocks (a leaf's B
+// block depends only on its binned lambda and internal-face mask, both part of
+// the cluster key).  rep_* index the representatives as clusters 0..nkc-1.
 template <class T>
-int build_precond_blocks(hps_handle* h, const double2* cdiag, const int* d_cl_leaf_begin, const int* d_cl_leaves,
-                         cudaStream_t st) {
+int build_precond_blocks(hps_handle* h, const int* d_rep_leaf_begin, const int* d_rep_leaves,
+                         const int* d_rep_slot_lf, const std::vector<int>& rep_leaf_begin, cudaStream_t st) {
   ClusterTables& ct = h->ct;
   const int n = h->n, ni = h->ni, nb = h->nb, q = h->q, q2 = q * q;
   int max_int = 0, max_leaves = 0;
-  for (int c = 0; c < ct.ncl; ++c) {
-    max_int = std::max(max_int, (ct.cl_slot_begin[c + 1] - ct.cl_slot_begin[c]) * q2);
-    max_leaves = std::max(max_leaves, ct.cl_leaf_begin[c + 1] - ct.cl_leaf_begin[c]);
+  for (int k = 0; k < ct.nkc; ++k) {
+    max_int = std::max(max_int, (ct.kc_slot_begin[k + 1] - ct.kc_slot_begin[k]) * q2);
+    max_leaves = std::max(max_leaves, rep_leaf_begin[k + 1] - rep_leaf_begin[k]);
   }
   const int ncols_l = n + nb, ld_l = ncols_l;
   const long long wl_stride = (long long)n * ld_l;
@@ -949,16 +1120,16 @@ int build_precond_blocks(hps_handle* h, const double2* cdiag, const int* d_cl_le
   HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
   GridDims gd{h->nx, h->ny, h->nz};
   int rc = HPS_OK;
-  for (int c0 = 0; c0 < ct.ncl && rc == HPS_OK; c0 += cb) {
-    const int nc = std::min(cb, ct.ncl - c0);
-    const int lb = ct.cl_leaf_begin[c0], le = ct.cl_leaf_begin[c0 + nc];
+  for (int c0 = 0; c0 < ct.nkc && rc == HPS_OK; c0 += cb) {
+    const int nc = std::min(cb, ct.nkc - c0);
+    const int lb = rep_leaf_begin[c0], le = rep_leaf_begin[c0 + nc];
     const int nlb = le - lb;
-    const int* leaf_ids = d_cl_leaves + lb;
+    const int* leaf_ids = d_rep_leaves + lb;
     auto body = [&]() -> int {
       HPS_CUDA_TRY(cudaMemsetAsync(Wl, 0, (size_t)wl_stride * nlb * sizeof(T), st));
       dim3 ga((n + 127) / 128, nlb);
       assemble_kernel<T><<<ga, 128, 0, st>>>(Wl, wl_stride, ld_l, leaf_ids, 0, nlb, h->tables, h->tl, h->eta,
-                                             cdiag, h->lambda, 1);
+                                             nullptr, h->lambda_q, 1);
       HPS_CUDA_TRY(cudaGetLastError());
       HPS_CUDA_TRY(run_gj(Wl, wl_stride, ld_l, n, ncols_l, ni, nlb, d_status, st));
       dim3 ge(256, nlb);
@@ -970,30 +1141,30 @@ int build_precond_blocks(hps_handle* h, const double2* cdiag, const int* d_cl_le
       extract_b_kernel<T><<<dim3(64, nlb), 256, 0, st>>>(Rt, (long long)nb * h->ldR, h->ldR, leaf_ids, nlb, q,
                                                          h->dct.int_mask, h->dct.b_off, h->B64, h->B32);
       HPS_CUDA_TRY(cudaGetLastError());
-      assemble_cluster_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
-                                                                h->dct.slot_lf, d_cl_leaf_begin, d_cl_leaves, Rt,
+      assemble_cluster_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.kc_slot_begin,
+                                                                d_rep_slot_lf, d_rep_leaf_begin, d_rep_leaves, Rt,
                                                                 (long long)nb * h->ldR, h->ldR, lb, gd, q);
       HPS_CUDA_TRY(cudaGetLastError());
-      // clusters of one size are eliminated in one launch
+      // blocks of one size are eliminated in one launch
       int cstart = c0;
       while (cstart < c0 + nc) {
-        const int sz = (ct.cl_slot_begin[cstart + 1] - ct.cl_slot_begin[cstart]) * q2;
+        const int sz = (ct.kc_slot_begin[cstart + 1] - ct.kc_slot_begin[cstart]) * q2;
         int cend = cstart + 1;
-        while (cend < c0 + nc && (ct.cl_slot_begin[cend + 1] - ct.cl_slot_begin[cend]) * q2 == sz) ++cend;
+        while (cend < c0 + nc && (ct.kc_slot_begin[cend + 1] - ct.kc_slot_begin[cend]) * q2 == sz) ++cend;
         if (sz > 0)
           HPS_CUDA_TRY(run_gj(Wc + (long long)(cstart - c0) * wc_stride, wc_stride, ldw, sz, 2 * sz, 0, cend - cstart,
                               d_status, st));
         cstart = cend;
       }
       if (h->Kc64 || h->Kc32) {
-        extract_kc_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
-                                                            h->dct.cl_kc_off, q, h->Kc64, h->Kc32);
+        extract_kc_kernel<T><<<dim3(256, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.kc_slot_begin,
+                                                            h->dct.kc_off, q, h->Kc64, h->Kc32);
         HPS_CUDA_TRY(cudaGetLastError());
       }
       if constexpr (std::is_same<T, float2>::value) {
         if (!h->Kc32 && h->Kc16) {
-          quantize_kc_ws_kernel<<<dim3(64, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.cl_slot_begin,
-                                                              h->dct.cl_kc_off, q2, h->Kc16, h->Kc16s);
+          quantize_kc_ws_kernel<<<dim3(64, nc), 256, 0, st>>>(Wc, wc_stride, ldw, c0, nc, h->dct.kc_slot_begin,
+                                                              h->dct.kc_off, q2, h->Kc16, h->Kc16s);
           HPS_CUDA_TRY(cudaGetLastError());
         }
       }
@@ -1010,41 +1181,87 @@ int build_precond_blocks(hps_handle* h, const double2* cdiag, const int* d_cl_le
   return rc;
 }
 
-int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+namespace {
+template <class V>
+int upload(hps_handle* h, V*& dst, const std::vector<V>& vec, cudaStream_t st) {
+  const size_t bytes = std::max<size_t>(1, vec.size()) * sizeof(V);
+  HPS_CUDA_TRY(cudaMalloc((void**)&dst, bytes));
+  h->bytes += bytes;
+  if (!vec.empty()) HPS_CUDA_TRY(cudaMemcpyAsync((void*)dst, vec.data(), vec.size() * sizeof(V), cudaMemcpyHostToDevice, st));
+  return HPS_OK;
+}
+}  // namespace
+
+int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
   ClusterTables& ct = h->ct;
-  // device copies of the tables
-  auto up = [&](auto*& dst, const auto& vec) -> int {
-    using E = std::remove_reference_t<decltype(vec[0])>;
-    const size_t bytes = std::max<size_t>(1, vec.size()) * sizeof(E);
-    HPS_CUDA_TRY(cudaMalloc((void**)&dst, bytes));
-    h->bytes += bytes;
-    if (!vec.empty())
-      HPS_CUDA_TRY(cudaMemcpyAsync((void*)dst, vec.data(), vec.size() * sizeof(E), cudaMemcpyHostToDevice, st));
-    return HPS_OK;
-  };
   int rc;
-  if ((rc = up(h->dct.slot_lf, ct.slot_lf))) return rc;
-  if ((rc = up(h->dct.slot_cluster, ct.slot_cluster))) return rc;
-  if ((rc = up(h->dct.cl_slot_begin, ct.cl_slot_begin))) return rc;
-  if ((rc = up(h->dct.cl_kc_off, ct.cl_kc_off))) return rc;
-  if ((rc = up(h->dct.lf_slot, ct.lf_slot))) return rc;
-  if ((rc = up(h->dct.int_mask, ct.int_mask))) return rc;
-  if ((rc = up(h->dct.b_off, ct.b_off))) return rc;
-  int* d_cl_leaf_begin = nullptr;
-  int* d_cl_leaves = nullptr;
-  HPS_CUDA_TRY(cudaMalloc(&d_cl_leaf_begin, ct.cl_leaf_begin.size() * sizeof(int)));
-  HPS_CUDA_TRY(cudaMalloc(&d_cl_leaves, ct.cl_leaves.size() * sizeof(int)));
-  HPS_CUDA_TRY(cudaMemcpyAsync(d_cl_leaf_begin, ct.cl_leaf_begin.data(), ct.cl_leaf_begin.size() * sizeof(int),
-                               cudaMemcpyHostToDevice, st));
-  HPS_CUDA_TRY(cudaMemcpyAsync(d_cl_leaves, ct.cl_leaves.data(), ct.cl_leaves.size() * sizeof(int),
-                               cudaMemcpyHostToDevice, st));
+  HPS_CUDA_TRY(cudaMalloc(&h->lambda_q, (size_t)h->nl * sizeof(double2)));
+  h->bytes += (size_t)h->nl * sizeof(double2);
   lambda_kernel<<<h->nl, 256, 0, st>>>(cdiag, h->ni, h->lambda);
   HPS_CUDA_TRY(cudaGetLastError());
-  rc = h->Kc64 ? build_precond_blocks<double2>(h, cdiag, d_cl_leaf_begin, d_cl_leaves, st)
-               : build_precond_blocks<float2>(h, cdiag, d_cl_leaf_begin, d_cl_leaves, st);
+  std::vector<double2> lam(h->nl);
+  HPS_CUDA_TRY(cudaMemcpyAsync(lam.data(), h->lambda, (size_t)h->nl * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  // binning: nearest multiple of w = lambda_bin * max |lambda| (ties to even)
+  double w = 0.0;
+  if (h->opt.lambda_bin > 0.0) {
+    double mx = 0.0;
+    for (const double2& l : lam) mx = std::max(mx, std::hypot(l.x, l.y));
+    w = h->opt.lambda_bin * mx;
+  }
+  std::vector<double2> lamq(lam);
+  if (w > 0.0)
+    for (double2& l : lamq) l = make_double2(w * std::nearbyint(l.x / w), w * std::nearbyint(l.y / w));
+  HPS_CUDA_TRY(cudaMemcpyAsync(h->lambda_q, lamq.data(), (size_t)h->nl * sizeof(double2), cudaMemcpyHostToDevice, st));
+  assign_blocks(h, &lamq);
+  if ((rc = upload(h, h->dct.slot_lf, ct.slot_lf, st))) return rc;
+  if ((rc = upload(h, h->dct.slot_cluster, ct.slot_cluster, st))) return rc;
+  if ((rc = upload(h, h->dct.cl_slot_begin, ct.cl_slot_begin, st))) return rc;
+  if ((rc = upload(h, h->dct.cl_kc_off, ct.cl_kc_off, st))) return rc;
+  if ((rc = upload(h, h->dct.lf_slot, ct.lf_slot, st))) return rc;
+  if ((rc = upload(h, h->dct.int_mask, ct.int_mask, st))) return rc;
+  if ((rc = upload(h, h->dct.b_off, ct.b_off, st))) return rc;
+  if ((rc = upload(h, h->dct.leaf_bcls, ct.leaf_bcls, st))) return rc;
+  if ((rc = upload(h, h->dct.bc_rep, ct.bc_rep, st))) return rc;
+  if ((rc = upload(h, h->dct.kc_off, ct.kc_off, st))) return rc;
+  if ((rc = upload(h, h->dct.kc_slot_begin, ct.kc_slot_begin, st))) return rc;
+  if ((rc = upload(h, h->dct.kslot_class, ct.kslot_class, st))) return rc;
+  if ((rc = upload(h, h->dct.kc_members, ct.kc_members, st))) return rc;
+  if ((rc = upload(h, h->dct.cl_tpos, ct.cl_tpos, st))) return rc;
+  if ((rc = upload(h, h->dct.lf_tpos, ct.lf_tpos, st))) return rc;
+  for (int i = 0; i < 4; ++i)
+    if ((rc = upload(h, h->dct.kitems[i], ct.kitems[i], st))) return rc;
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  return HPS_OK;
+}
+
+int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+  (void)cdiag;
+  const ClusterTables& ct = h->ct;
+  // the representative cluster of every distinct K block, as clusters 0..nkc-1
+  std::vector<int> rep_leaf_begin(1, 0), rep_leaves, rep_slot_lf;
+  for (int k = 0; k < ct.nkc; ++k) {
+    const int c = ct.kc_rep[k];
+    for (int l = ct.cl_leaf_begin[c]; l < ct.cl_leaf_begin[c + 1]; ++l) rep_leaves.push_back(ct.cl_leaves[l]);
+    rep_leaf_begin.push_back((int)rep_leaves.size());
+    for (int sl = ct.cl_slot_begin[c]; sl < ct.cl_slot_begin[c + 1]; ++sl) rep_slot_lf.push_back(ct.slot_lf[sl]);
+  }
+  int *d_leaf_begin = nullptr, *d_leaves = nullptr, *d_slot_lf = nullptr;
+  auto dev = [&](int*& d, const std::vector<int>& v) -> int {
+    HPS_CUDA_TRY(cudaMalloc(&d, std::max<size_t>(1, v.size()) * sizeof(int)));
+    if (!v.empty()) HPS_CUDA_TRY(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    return HPS_OK;
+  };
+  int rc = dev(d_leaf_begin, rep_leaf_begin);
+  if (!rc) rc = dev(d_leaves, rep_leaves);
+  if (!rc) rc = dev(d_slot_lf, rep_slot_lf);
+  if (!rc)
+    rc = h->Kc64 ? build_precond_blocks<double2>(h, d_leaf_begin, d_leaves, d_slot_lf, rep_leaf_begin, st)
+                 : build_precond_blocks<float2>(h, d_leaf_begin, d_leaves, d_slot_lf, rep_leaf_begin, st);
   cudaStreamSynchronize(st);
-  cudaFree(d_cl_leaf_begin);
-  cudaFree(d_cl_leaves);
+  if (d_leaf_begin) cudaFree(d_leaf_begin);
+  if (d_leaves) cudaFree(d_leaves);
+  if (d_slot_lf) cudaFree(d_slot_lf);
   return rc;
 }
 

@@ -22,6 +22,11 @@ import numpy as np
 
 
 def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
+    """One entry of Table PlaneMinErr (Sec. 6.2): the modulated plane wave of eq. (plane) with
+    the bump medium, n_c = p, solved in the FP64 form to tol, E_h over all N = N_l (n_i + n_b)
+    leaf unknowns (interior and Chebyshev face nodes).  kappa = 2 pi (12 L) / ppw: 12 points
+    per leaf and axis, the count the paper's tables imply for n_c = 16 (48 points per axis on
+    4^3 leaves at 3 wavelengths and 16 ppw)."""
     import torch
 
     import workloads as W
@@ -29,20 +34,23 @@ def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
     from . import Solver, face_normals, nodes
     kappa = 2.0 * math.pi * 12.0 * L / ppw
     w = W.manufactured(L=L, p=p, kappa=kappa)
-    xi, xf = nodes(L, L, L, p)
+    xi, xf, xc = nodes(L, L, L, p, cheb_faces=True)
     nrm = np.broadcast_to(face_normals()[None, :, None, :], xf.shape)
     s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
     t = torch.from_numpy(w.sample_t(xf, nrm).reshape(-1)).cuda()
     solver = Solver(L, L, L, p, kappa=kappa, eta=kappa, b=w.sample_b(xi), forms=("fp64",), cluster=0)
     try:
         f, info = solver.solve(s=s, t=t, tol=tol, form="fp64")
-        u = solver.recover(f, s=s).cpu().numpy()
+        u, uf = solver.recover(f, s=s, faces=True)
+        u, uf = u.cpu().numpy(), uf.cpu().numpy()
     finally:
         solver.close()
-    u_exact = w.meta["u"](xi).reshape(-1)
-    e_h = float(np.linalg.norm(u - u_exact) / np.linalg.norm(u_exact))
-    return {"leaves": L, "ppw": ppw, "kappa": kappa, "E_h": e_h, "iterations": info["iterations"],
-            "rel_residual": info["rel_residual"]}
+    ue, ufe = w.meta["u"](xi).reshape(-1), w.meta["u"](xc).reshape(-1)
+    e_int = float(np.linalg.norm(u - ue) / np.linalg.norm(ue))
+    num = np.linalg.norm(u - ue) ** 2 + np.linalg.norm(uf - ufe) ** 2
+    den = np.linalg.norm(ue) ** 2 + np.linalg.norm(ufe) ** 2
+    return {"leaves": L, "ppw": ppw, "kappa": kappa, "E_h": float(np.sqrt(num / den)), "E_h_interior": e_int,
+            "iterations": info["iterations"], "rel_residual": info["rel_residual"]}
 
 
 def large_solve(L=32, steps=3, warmup=1):
@@ -137,13 +145,69 @@ def multi_rhs(L=16, nrhs=64, restart=30, steps=2, warmup=1, precond=False):
             "phase_ms_per_solve": {k: v / steps for k, v in prof["ms"].items()}}
 
 
+def precond_sharing(L=16, bins=(0.0, 0.001, 0.01, 0.05), steps=2, warmup=1):
+    """Shared preconditioner blocks on the bump workload (16^3 leaves, p = 10, kappa = 40):
+    for each bin width of the homogenized constants (relative to max |lambda|), the distinct
+    K_c / B blocks, setup time, iterations and time per mixed-form solve (FP16 blocks).  The
+    solutions agree to the tolerance whatever the bins."""
+    import time
+
+    import torch
+
+    import workloads as W
+
+    from . import Solver, nodes
+    w = W.bump_16cubed(L=L)
+    xi, xf = nodes(L, L, L, w.p)
+    b = w.sample_b(xi)
+    s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
+    rows = []
+    ref = None
+    for delta in bins:
+        t0 = time.time()
+        solver = Solver(L, L, L, w.p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",), lambda_bin=delta)
+        torch.cuda.synchronize()
+        setup_s = time.time() - t0
+        try:
+            out = torch.empty(solver.nf, dtype=torch.complex128, device="cuda")
+            for _ in range(warmup):
+                solver.solve(s=s, tol=w.tol, form="mixed", out=out)
+            solver.profile(enable=True, reset=True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                _, info = solver.solve(s=s, tol=w.tol, form="mixed", out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            prof = solver.profile(enable=False, reset=True)
+            ncl, kb, bb = solver.precond_info()
+            mem = solver.memory_bytes
+        finally:
+            solver.close()
+        if ref is None:
+            ref = out.clone()
+        diff = float(torch.linalg.norm(out - ref).item() / torch.linalg.norm(ref).item())
+        rows.append({"lambda_bin": delta, "clusters": ncl, "distinct_K": kb, "distinct_B": bb, "setup_s": setup_s,
+                     "device_bytes": mem, "iterations": info["iterations"], "ms_per_solve": ms,
+                     "unknowns_per_s": solver.nf / (ms / 1e3), "rel_diff_vs_first": diff,
+                     "phase_ms_per_solve": {k: v / steps for k, v in prof["ms"].items()}})
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L", type=int, default=4)
     ap.add_argument("--ppw", type=float, nargs="*", default=[24.0, 19.2, 16.0, 12.0, 9.6])
     ap.add_argument("--large", action="store_true", help="run the 32^3-leaf large solve instead")
     ap.add_argument("--multi-rhs", action="store_true", help="run the 64-RHS tensor-core workload instead")
+    ap.add_argument("--sharing", action="store_true", help="run the shared-preconditioner-block sweep instead")
     args = ap.parse_args()
+    if args.sharing:
+        for row in precond_sharing(L=args.L if args.L != 4 else 16):
+            print(json.dumps(row), flush=True)
+        return
     if args.large:
         print(json.dumps(large_solve()), flush=True)
         return

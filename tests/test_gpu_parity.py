@@ -164,10 +164,17 @@ def test_recover_interior_matches_oracle(ragged):
     w, oc, solver, (xi, xf, b, s, t) = ragged
     sd = torch.from_numpy(s.reshape(-1)).cuda()
     f, info = solver.solve(s=sd, t=torch.from_numpy(t.reshape(-1)).cuda(), tol=1e-12, form="fp64")
-    u = solver.recover(f, s=sd).cpu().numpy().reshape(oc.grid.nleaves, -1)
-    ref = O.recover_interior(oc.grid, w.kappa, w.eta, oc.b, oc.s[0], oc.solve())
+    u, uf = solver.recover(f, s=sd, faces=True)
+    u = u.cpu().numpy().reshape(oc.grid.nleaves, -1)
+    uf = uf.cpu().numpy().reshape(oc.grid.nleaves, -1)
+    ref, ref_f = O.recover_interior(oc.grid, w.kappa, w.eta, oc.b, oc.s[0], oc.solve(), with_faces=True)
     assert rel(u, ref) < 1e-10
+    assert rel(uf, ref_f) < 1e-10
     assert rel(u, w.meta["u"](oc.xi)) < 1e-2
+    _, _, xc = hps.nodes(w.nx, w.ny, w.nz, w.p, cheb_faces=True)
+    assert np.abs(xc - O.cheb_face_nodes(oc.grid)).max() < 1e-15
+    # face nodes sit where the p = 7 interpolant is least accurate: a looser sanity bar
+    assert rel(uf, w.meta["u"](xc).reshape(oc.grid.nleaves, -1)) < 3e-2
 
 
 def test_solve_host_buffers_match_device_buffers(ragged):

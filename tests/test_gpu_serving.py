@@ -42,4 +42,11 @@ def test_budget_limits_concurrency():
     srv = Server(be, hbm_budget=need, max_active=4)
     res = srv.run(reqs)
     assert all(r.error is None for r in res)
-    assert srv.peak_bytes <= need and srv.peak_active == 1
+    assert srv.peak_bytes <= need
+    # copies of the largest request: one fits at a time
+    big = max(reqs, key=lambda r: be.bytes_needed(r.workload))
+    same = [Request(i, big.workload, 0.001 * i) for i in range(3)]
+    srv1 = Server(be, hbm_budget=need, max_active=4)
+    res1 = srv1.run(same)
+    assert all(r.error is None for r in res1)
+    assert srv1.peak_active == 1 and srv1.peak_bytes == need
