@@ -115,7 +115,8 @@ void free_handle(hps_handle* h) {
                   h->dct.slot_lf, h->dct.slot_cluster, h->dct.cl_slot_begin, h->dct.cl_kc_off, h->dct.lf_slot,
                   h->dct.int_mask, h->dct.b_off, h->dct.leaf_bcls, h->dct.bc_rep, h->dct.kc_off,
                   h->dct.kc_slot_begin, h->dct.kslot_class, h->dct.kc_members, h->dct.kitems[0], h->dct.kitems[1],
-                  h->dct.kitems[2], h->dct.kitems[3], h->dct.cl_tpos, h->dct.lf_tpos};
+                  h->dct.kitems[2], h->dct.kitems[3], h->dct.cl_tpos, h->dct.lf_tpos, h->dct.brd, h->dct.bto,
+                  h->dct.bsc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -364,6 +365,8 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
     bytes += (size_t)h.nl * (2 * sizeof(int) + c16) + ct.kc_off.size() * sizeof(long long) +
              (ct.kc_slot_begin.size() + ct.kslot_class.size() + ct.kc_members.size()) * sizeof(int);
     for (const auto& v : ct.kitems) bytes += std::max<size_t>(1, v.size()) * sizeof(int4);
+    bytes += (size_t)h.nl * 6 * 3 * sizeof(int) + (size_t)ct.ncl * sizeof(long long) +
+             (size_t)h.nl * 6 * sizeof(long long);  // stage-B offsets, t positions
     if (want64) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c16;
     if (want32) bytes += (size_t)((o.lean ? 0 : ct.kc_elems) + ct.b_elems) * c8;
     if (want32 && (o.precond_fp16 || o.lean))

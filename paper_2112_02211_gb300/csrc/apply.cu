@@ -215,13 +215,13 @@ struct PrecBP {
   using Acc = typename MT<TM>::Acc;
   struct Args {
     const TM* B;
-    const float* bscale;  // FP16 blocks: row scales, index (bcls[leaf]*6 + face)*q2 + j
-    const int* bcls;
+    const float* bscale;  // FP16 blocks: row scales, index bsc[leaf*6 + k] + j
     const long long* b_off;
     const uint8_t* int_mask;
-    const long long* lf_tpos;
+    const int* brd;  // per leaf, internal faces then external: input offsets
+    const int* bto;  // per leaf, internal faces: t offsets
+    const int* bsc;  // per leaf, internal faces: row-scale bases
     int nb, q2;
-    GridDims g;
     const TIN* r;
     TOUT* z;
     TOUT* t;
@@ -230,13 +230,12 @@ struct PrecBP {
     long long nitems;
   };
   // One item per leaf: the rows of all its internal faces (B^leaf) against the
-  // values on its external faces, plus the copy of the external faces.
+  // values on its external faces, plus the copy of the external faces.  The
+  // offsets of the faces involved come from per-leaf tables.
   __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
     it.leaf = (int)item;
-    const int mask = A.int_mask[it.leaf];
-    it.mask = mask;
-    it.xoff = (long long)it.leaf * A.nb;
-    const int nint = __popc(mask);
+    const int nint = __popc((unsigned)A.int_mask[it.leaf]);
+    it.mask = nint;
     if (nint == 0) return false;
     it.nrows = nint * A.q2;
     it.ncols = (6 - nint) * A.q2;
@@ -244,39 +243,29 @@ struct PrecBP {
     it.mat = A.B + A.b_off[it.leaf];
     return true;
   }
-  // k-th set (internal) or clear (external) face bit of the mask
-  __device__ static int nth_face(int mask, int k, bool internal) {
-    for (int f = 0; f < 6; ++f)
-      if (((mask >> f) & 1) == (internal ? 1 : 0)) {
-        if (k == 0) return f;
-        --k;
-      }
-    return 5;
-  }
   __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
-    const int f = nth_face(it.mask, c / A.q2, false);
-    return cvt<Acc>(A.r[rhs * A.nf + it.xoff + (long long)f * A.q2 + c % A.q2]);
+    const int k = c / A.q2;
+    return cvt<Acc>(A.r[rhs * A.nf + A.brd[it.leaf * 6 + it.mask + k] + (c - k * A.q2)]);
   }
   __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
     for (int idx = tid; idx < nr * it.nrows; idx += kThreads) {
       const int rhs = idx / it.nrows, row = idx % it.nrows;
-      const int face = nth_face(it.mask, row / A.q2, true), j = row % A.q2;
-      const int nbr = A.g.neighbor(it.leaf, face);
-      const long long aoff = (long long)nbr * A.nb + (long long)(face ^ 1) * A.q2;
-      const long long ooff = A.lf_tpos[nbr * 6 + (face ^ 1)];
-      const Acc g = rscale(outs[idx], A.bscale, ((long long)A.bcls[it.leaf] * 6 + face) * A.q2 + j);
-      const Acc v = csub(cvt<Acc>(A.r[rhs * A.nf + aoff + j]), g);
-      A.t[rhs * A.tstride + ooff + j] = cvt<TOUT>(v);
+      const int k = row / A.q2, j = row - k * A.q2;
+      const int e = it.leaf * 6 + k;
+      const Acc g = rscale(outs[idx], A.bscale, (long long)A.bsc[e] + j);
+      const Acc v = csub(cvt<Acc>(A.r[rhs * A.nf + A.brd[e] + j]), g);
+      A.t[rhs * A.tstride + A.bto[e] + j] = cvt<TOUT>(v);
     }
     copy(A, it, nr, tid);
   }
   // z = r on the faces leaving the leaf's cluster
   __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
-    const int next = 6 - __popc(it.mask);
-    for (int idx = tid; idx < nr * next * A.q2; idx += kThreads) {
-      const int rhs = idx / (next * A.q2), e = idx % (next * A.q2);
-      const int face = nth_face(it.mask, e / A.q2, false);
-      const long long o = rhs * A.nf + it.xoff + (long long)face * A.q2 + e % A.q2;
+    const int nint = __popc((unsigned)A.int_mask[it.leaf]);
+    const int n = (6 - nint) * A.q2;
+    for (int idx = tid; idx < nr * n; idx += kThreads) {
+      const int rhs = idx / n, e = idx % n;
+      const int k = e / A.q2;
+      const long long o = rhs * A.nf + A.brd[it.leaf * 6 + nint + k] + (e - k * A.q2);
       A.z[o] = cvt<TOUT>(cvt<Acc>(A.r[o]));
     }
   }
@@ -494,13 +483,13 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     typename P::Args A;
     A.B = B;
     A.bscale = bscale;
-    A.bcls = h->dct.leaf_bcls;
     A.b_off = h->dct.b_off;
     A.int_mask = h->dct.int_mask;
-    A.lf_tpos = h->dct.lf_tpos;
+    A.brd = h->dct.brd;
+    A.bto = h->dct.bto;
+    A.bsc = h->dct.bsc;
     A.nb = h->nb;
     A.q2 = q2;
-    A.g = GridDims{h->nx, h->ny, h->nz};
     A.r = r;
     A.z = z;
     A.t = t;

@@ -100,6 +100,12 @@ struct ClusterTables {
   std::vector<long long> cl_tpos;
   std::vector<long long> lf_tpos;
   long long tsize = 0;
+  // stage-B offsets per leaf, 6 entries each (internal faces first, then
+  // external, in face order): bface = face index; brd = input offset of the
+  // neighbour's slot across an internal face (nbr*nb + (face^1)*q^2) or of the
+  // leaf's own external face (leaf*nb + face*q^2); bto = t offset of that
+  // neighbour slot (internal faces); bsc = FP16 row-scale base (bcls*6 + face)*q^2
+  std::vector<int> brd, bto, bsc;
   long long kc_elems = 0, b_elems = 0;
 };
 
@@ -120,6 +126,9 @@ struct DeviceClusterTables {
   int4* kitems[4] = {nullptr, nullptr, nullptr, nullptr};
   long long* cl_tpos = nullptr;
   long long* lf_tpos = nullptr;
+  int* brd = nullptr;
+  int* bto = nullptr;
+  int* bsc = nullptr;
 };
 
 // Per-phase CUDA-event timing and a launch counter (see hps_profile).

@@ -420,57 +420,72 @@ struct GivensArgs {
   int* any_active;
 };
 
-// One thread per right-hand side: finish column j of the Hessenberg matrix,
-// apply the previous rotations, make the new one, update g.
+// Finish column j of the Hessenberg matrix, apply the previous rotations, make
+// the new one, update g.  One block of 64 threads per right-hand side: the new
+// column and the stored rotations are staged in shared memory in parallel,
+// thread 0 applies the rotations (a dependent chain) there, and the column is
+// written back in parallel.  Requires m + 1 < 64 (restart <= 60).
 __global__ void givens_kernel(GivensArgs a) {
-  const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
-  if (rhs >= a.nrhs) return;
-  if (!a.active[rhs]) return;
-  const int j = a.j;
-  // ||w||^2 was reduced into the spare last slot of hcol
-  const double nrm2 = a.hcol[(long long)rhs * (a.M1 + 1) + a.M1].x;
-  const double hn = sqrt(nrm2);
-  double2* Hc = a.H + (long long)rhs * a.M1 * a.m;  // Hc[i*m + j]
-  for (int i = 0; i <= j; ++i) Hc[i * a.m + j] = cadd(a.hcol[(long long)rhs * (a.M1 + 1) + i], a.h2[(long long)rhs * a.M1 + i]);
-  Hc[(j + 1) * a.m + j] = make_double2(hn, 0.0);
+  const int rhs = blockIdx.x;
+  if (rhs >= a.nrhs || !a.active[rhs]) return;
+  __shared__ double2 col[64];
+  __shared__ double csv[64];
+  __shared__ double2 snv[64];
+  const int j = a.j, t = threadIdx.x;
+  const double2* hc = a.hcol + (long long)rhs * (a.M1 + 1);
+  const double2* h2 = a.h2 + (long long)rhs * a.M1;
   double* cs = a.cs + (long long)rhs * a.m;
   double2* sn = a.sn + (long long)rhs * a.m;
-  for (int i = 0; i < j; ++i) {
-    const double2 x = Hc[i * a.m + j], y = Hc[(i + 1) * a.m + j];
-    Hc[i * a.m + j] = cadd(cscale(x, cs[i]), cmul(sn[i], y));
-    const double2 sc = make_double2(sn[i].x, -sn[i].y);
-    Hc[(i + 1) * a.m + j] = csub(cscale(y, cs[i]), cmul(sc, x));
+  if (t <= j) col[t] = cadd(hc[t], h2[t]);
+  if (t < j) {
+    csv[t] = cs[t];
+    snv[t] = sn[t];
   }
-  const double2 x = Hc[j * a.m + j], y = Hc[(j + 1) * a.m + j];
-  const double ax = sqrt(cabs2(x)), den = sqrt(cabs2(x) + cabs2(y));
-  double c;
-  double2 s;
-  if (ax == 0.0) {
-    c = 0.0;
-    s = make_double2(1.0, 0.0);
-  } else {
-    c = ax / den;
-    const double2 ph = cscale(x, 1.0 / ax);
-    s = cscale(cmul(ph, make_double2(y.x, -y.y)), 1.0 / den);
+  __syncthreads();
+  if (t == 0) {
+    // ||w||^2 was reduced into the spare last slot of hcol
+    const double hn = sqrt(hc[a.M1].x);
+    col[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const double2 x = col[i], y = col[i + 1];
+      col[i] = cadd(cscale(x, csv[i]), cmul(snv[i], y));
+      const double2 sc = make_double2(snv[i].x, -snv[i].y);
+      col[i + 1] = csub(cscale(y, csv[i]), cmul(sc, x));
+    }
+    const double2 x = col[j], y = col[j + 1];
+    const double ax = sqrt(cabs2(x)), den = sqrt(cabs2(x) + cabs2(y));
+    double c;
+    double2 sv;
+    if (ax == 0.0) {
+      c = 0.0;
+      sv = make_double2(1.0, 0.0);
+    } else {
+      c = ax / den;
+      const double2 ph = cscale(x, 1.0 / ax);
+      sv = cscale(cmul(ph, make_double2(y.x, -y.y)), 1.0 / den);
+    }
+    cs[j] = c;
+    sn[j] = sv;
+    col[j] = cadd(cscale(x, c), cmul(sv, y));
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2* g = a.g + (long long)rhs * a.M1;
+    const double2 gj = g[j];
+    g[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));  // -conj(s) g_j
+    g[j] = cscale(gj, c);
+    const double e = sqrt(cabs2(g[j + 1]));
+    a.est[rhs] = e;
+    a.kcount[rhs] = j + 1;
+    const bool breakdown = !(hn > 1e-300 * fmax(1.0, den));
+    a.invn[rhs] = breakdown ? 0.0 : 1.0 / hn;
+    if (breakdown || e <= a.target[rhs] || j + 1 >= a.m) {
+      a.active[rhs] = 0;
+    } else {
+      atomicOr(a.any_active, 1);
+    }
   }
-  cs[j] = c;
-  sn[j] = s;
-  Hc[j * a.m + j] = cadd(cscale(x, c), cmul(s, y));
-  Hc[(j + 1) * a.m + j] = make_double2(0.0, 0.0);
-  double2* g = a.g + (long long)rhs * a.M1;
-  const double2 gj = g[j];
-  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-  g[j] = cscale(gj, c);
-  const double e = sqrt(cabs2(g[j + 1]));
-  a.est[rhs] = e;
-  a.kcount[rhs] = j + 1;
-  const bool breakdown = !(hn > 1e-300 * fmax(1.0, den));
-  a.invn[rhs] = breakdown ? 0.0 : 1.0 / hn;
-  if (breakdown || e <= a.target[rhs] || j + 1 >= a.m) {
-    a.active[rhs] = 0;
-  } else {
-    atomicOr(a.any_active, 1);
-  }
+  __syncthreads();
+  double2* Hc = a.H + (long long)rhs * a.M1 * a.m;  // Hc[i*m + j]
+  if (t <= j + 1) Hc[t * a.m + j] = col[t];
 }
 
 // w <- w * invn[rhs]
@@ -787,7 +802,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       ga.kcount = kcount;
       ga.target = target;
       ga.any_active = any_active;
-      givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(ga);
+      givens_kernel<<<nrhs, 64, 0, st>>>(ga);
       HPS_CUDA_TRY(cudaGetLastError());
       if (mixed) scale_df_kernel<<<vgrid, 256, 0, st>>>((float4*)w, nf, invn);
       else scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);

@@ -1056,6 +1056,30 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
     }
     ct.tsize = round_up(std::max<long long>(pos, 1), 16);
   }
+  // stage-B offsets
+  ct.brd.assign((size_t)h->nl * 6, 0);
+  ct.bto.assign((size_t)h->nl * 6, 0);
+  ct.bsc.assign((size_t)h->nl * 6, 0);
+  for (int leaf = 0; leaf < h->nl; ++leaf) {
+    const int ix = leaf % h->nx, iy = (leaf / h->nx) % h->ny, iz = leaf / (h->nx * h->ny);
+    int k = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int f = 0; f < 6; ++f) {
+        const bool internal = (ct.int_mask[leaf] >> f) & 1;
+        if (internal != (pass == 0)) continue;
+        const size_t e = (size_t)leaf * 6 + k++;
+        if (internal) {
+          int c3[3] = {ix, iy, iz};
+          c3[f >> 1] += (f & 1) ? 1 : -1;
+          const int nbr = c3[0] + h->nx * (c3[1] + h->ny * c3[2]);
+          ct.brd[e] = nbr * h->nb + (f ^ 1) * q2;
+          ct.bto[e] = (int)ct.lf_tpos[(size_t)nbr * 6 + (f ^ 1)];
+          ct.bsc[e] = (ct.leaf_bcls[leaf] * 6 + f) * q2;
+        } else {
+          ct.brd[e] = leaf * h->nb + f * q2;
+        }
+      }
+  }
   // blocks for the tensor-core path: many members, an even row length (16-byte
   // aligned member rows of complex floats)
   ct.kc_tc.clear();
@@ -1229,6 +1253,9 @@ int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st
   if ((rc = upload(h, h->dct.kc_members, ct.kc_members, st))) return rc;
   if ((rc = upload(h, h->dct.cl_tpos, ct.cl_tpos, st))) return rc;
   if ((rc = upload(h, h->dct.lf_tpos, ct.lf_tpos, st))) return rc;
+  if ((rc = upload(h, h->dct.brd, ct.brd, st))) return rc;
+  if ((rc = upload(h, h->dct.bto, ct.bto, st))) return rc;
+  if ((rc = upload(h, h->dct.bsc, ct.bsc, st))) return rc;
   for (int i = 0; i < 4; ++i)
     if ((rc = upload(h, h->dct.kitems[i], ct.kitems[i], st))) return rc;
   HPS_CUDA_TRY(cudaStreamSynchronize(st));

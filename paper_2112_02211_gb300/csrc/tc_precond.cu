@@ -10,13 +10,14 @@
 //
 // As in the multi-RHS apply (tc_apply.cu): K_c's interleaved complex FP32
 // storage is read as a real n x 2n matrix A; the B operand rows are conj(t_m)
-// and the re/im swap of t_m, so A B = [Re Z | Im Z]; three TF32 products keep
-// FP32-level accuracy; FP32 accumulation in TMEM.
+// and the re/im swap of t_m, so A B = [Re Z | Im Z].  One TF32 product per
+// term (both operands rounded to TF32, 2^-11 relative, the precision of the
+// FP16 blocks used for the other clusters); FP32 accumulation in TMEM.
 //
 // Kernel (one CTA per SM, persistent over items = (128-row tile, 64-member tile)):
 //   warp 0       TMA producer: A tile (128 rows x 32 floats) and T tile
-//                (64 members x 32 floats), 128-byte swizzle, 3-stage ring
-//   warps 2..7   split into TF32 hi/lo operands (conj/swap rows of B)
+//                (64 members x 32 floats), 128-byte swizzle, 5-stage ring
+//   warps 2..7   round A to TF32 in place, build the conj/swap rows of B
 //   warp 1       TMEM allocation (256 columns, two accumulators); one lane
 //                issues the MMAs and commits to mbarriers
 //   warps 8..11  epilogue: TMEM -> registers -> z at each member cluster's
@@ -39,7 +40,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kStages = 3;
+constexpr int kStages = 5;
 constexpr int kTileM = 128;
 constexpr int kMem = 64;        // member clusters per tile
 constexpr int kTileN = 2 * kMem;  // (re, im) columns
@@ -47,8 +48,8 @@ constexpr int kTileK = 32;      // floats per K block (128 bytes)
 constexpr int kABytes = kTileM * kTileK * 4;  // 16 KB
 constexpr int kTBytes = kMem * kTileK * 4;    // 8 KB
 constexpr int kBBytes = kTileN * kTileK * 4;  // 16 KB
-// stage layout (each part 1024-byte aligned): Ahi(=A) | Alo | Bhi | Blo | T
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes + kTBytes;  // 72 KB
+// stage layout (each part 1024-byte aligned): A | B | T
+constexpr int kStageBytes = kABytes + kBBytes + kTBytes;  // 40 KB
 constexpr int kThreads = 384;
 constexpr int kTmemCols = 256;
 
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char* st = ring + s * kStageBytes;
           mbar_expect_tx(&bars->full[s], kABytes + kTBytes);
           tma_load_2d(st, &mapA, &bars->full[s], kb * kTileK, mt * kTileM);
-          tma_load_2d(st + 2 * kABytes + 2 * kBBytes, &mapT, &bars->full[s], kb * kTileK, nt * kMem);
+          tma_load_2d(st + kABytes + kBBytes, &mapT, &bars->full[s], kb * kTileK, nt * kMem);
         }
       }
       for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j)
@@ -146,30 +147,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           goto split_done;
         }
         unsigned char* st = ring + s * kStageBytes;
-        float4* Ahi = reinterpret_cast<float4*>(st);
-        float4* Alo = reinterpret_cast<float4*>(st + kABytes);
-        float4* Bhi = reinterpret_cast<float4*>(st + 2 * kABytes);
-        float4* Blo = reinterpret_cast<float4*>(st + 2 * kABytes + kBBytes);
-        const float4* T = reinterpret_cast<const float4*>(st + 2 * kABytes + 2 * kBBytes);
+        float4* A = reinterpret_cast<float4*>(st);
+        float4* B = reinterpret_cast<float4*>(st + kABytes);
+        const float4* T = reinterpret_cast<const float4*>(st + kABytes + kBBytes);
         for (int c = t; c < kABytes / 16; c += 192) {
-          const float4 v = Ahi[c];
-          const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-          Ahi[c] = h;
-          Alo[c] = make_float4(tf32_hi(v.x - h.x), tf32_hi(v.y - h.y), tf32_hi(v.z - h.z), tf32_hi(v.w - h.w));
+          const float4 v = A[c];
+          A[c] = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
         }
         // B row m = conj(t_m), B row 64 + m = swap(t_m): same 16-byte chunk positions
         for (int c = t; c < kTBytes / 16; c += 192) {
           const float4 v = T[c];
-          const float4 cj = make_float4(v.x, -v.y, v.z, -v.w);
-          const float4 sw = make_float4(v.y, v.x, v.w, v.z);
-          const float4 cjh = make_float4(tf32_hi(cj.x), tf32_hi(cj.y), tf32_hi(cj.z), tf32_hi(cj.w));
-          const float4 swh = make_float4(tf32_hi(sw.x), tf32_hi(sw.y), tf32_hi(sw.z), tf32_hi(sw.w));
-          Bhi[c] = cjh;
-          Blo[c] = make_float4(tf32_hi(cj.x - cjh.x), tf32_hi(cj.y - cjh.y), tf32_hi(cj.z - cjh.z),
-                               tf32_hi(cj.w - cjh.w));
-          Bhi[c + kTBytes / 16] = swh;
-          Blo[c + kTBytes / 16] = make_float4(tf32_hi(sw.x - swh.x), tf32_hi(sw.y - swh.y), tf32_hi(sw.z - swh.z),
-                                              tf32_hi(sw.w - swh.w));
+          B[c] = make_float4(tf32_hi(v.x), tf32_hi(-v.y), tf32_hi(v.z), tf32_hi(-v.w));
+          B[c + kTBytes / 16] = make_float4(tf32_hi(v.y), tf32_hi(v.x), tf32_hi(v.w), tf32_hi(v.z));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -203,14 +192,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t base = smem_u32(ring + s * kStageBytes);
-          const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes, blo = bhi + kBBytes;
+          const uint32_t aa = base, bb = base + kABytes;
 #pragma unroll
           for (int kk = 0; kk < kTileK / 8; ++kk) {
             const uint32_t off = kk * 32;
-            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_tf32(acc, smem_desc(ahi + off), smem_desc(bhi + off), idesc, first);
-            mma_tf32(acc, smem_desc(ahi + off), smem_desc(blo + off), idesc, 1u);
-            mma_tf32(acc, smem_desc(alo + off), smem_desc(bhi + off), idesc, 1u);
+            mma_tf32(acc, smem_desc(aa + off), smem_desc(bb + off), idesc, (kb == 0 && kk == 0) ? 0u : 1u);
           }
           mma_commit(&bars->empty[s]);
         }

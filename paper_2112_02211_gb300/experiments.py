@@ -21,36 +21,56 @@ import math
 import numpy as np
 
 
-def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
-    """One entry of Table PlaneMinErr (Sec. 6.2): the modulated plane wave of eq. (plane) with
-    the bump medium, n_c = p, solved in the FP64 form to tol, E_h over all N = N_l (n_i + n_b)
-    leaf unknowns (interior and Chebyshev face nodes).  kappa = 2 pi (12 L) / ppw: 12 points
-    per leaf and axis, the count the paper's tables imply for n_c = 16 (48 points per axis on
-    4^3 leaves at 3 wavelengths and 16 ppw)."""
+# Residual reduction that reaches the discretization's accuracy (Table PlaneResRed, Sec. 6.2),
+# by points per wavelength.
+RPRR = {24.0: 1e-13, 19.2: 1e-12, 16.0: 1e-10, 12.0: 1e-9, 9.6: 1e-8}
+
+
+def accuracy_case(kind="plane", L=4, p=16, ppw=24.0, tol=1e-13):
+    """One entry of the accuracy tables of Sec. 6.2-6.3: the modulated plane wave of eq. (plane)
+    (kind "plane": Tables PlaneMinErr, PlaneResRed) or the bumps solution of eq. (bumps) (kind
+    "bumps": Tables BumpsMinErr2, BumpsMinErr), both in the bump medium of eq. (source), n_c = p.
+    Solved in the FP64 form twice: to `tol` (E_h, the discretization's accuracy) and to the
+    table's residual reduction RPRR (E_h^it); E_h over all N = N_l (n_i + n_b) leaf unknowns
+    (interior and Chebyshev face nodes).  kappa = 2 pi (12 L) / ppw: 12 points per leaf and
+    axis, the count the paper's tables imply for n_c = 16 (48 points per axis on 4^3 leaves at
+    3 wavelengths and 16 ppw)."""
     import torch
 
     import workloads as W
 
     from . import Solver, face_normals, nodes
     kappa = 2.0 * math.pi * 12.0 * L / ppw
-    w = W.manufactured(L=L, p=p, kappa=kappa)
+    make = W.manufactured if kind == "plane" else W.manufactured_bumps
+    w = make(L=L, p=p, kappa=kappa)
     xi, xf, xc = nodes(L, L, L, p, cheb_faces=True)
     nrm = np.broadcast_to(face_normals()[None, :, None, :], xf.shape)
     s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
     t = torch.from_numpy(w.sample_t(xf, nrm).reshape(-1)).cuda()
-    solver = Solver(L, L, L, p, kappa=kappa, eta=kappa, b=w.sample_b(xi), forms=("fp64",), cluster=0)
+    rprr = RPRR.get(ppw, 1e-10)
+    solver = Solver(L, L, L, p, kappa=kappa, eta=kappa, b=w.sample_b(xi), forms=("fp64",), cluster=0, max_rhs=2)
     try:
-        f, info = solver.solve(s=s, t=t, tol=tol, form="fp64")
-        u, uf = solver.recover(f, s=s, faces=True)
-        u, uf = u.cpu().numpy(), uf.cpu().numpy()
+        f1, info1 = solver.solve(s=s, t=t, tol=tol, form="fp64")
+        f2, info2 = solver.solve(s=s, t=t, tol=rprr, form="fp64")
+        u, uf = solver.recover(torch.cat([f1, f2]), s=torch.cat([s, s]), nrhs=2, faces=True)
+        u, uf = u.cpu().numpy().reshape(2, -1), uf.cpu().numpy().reshape(2, -1)
     finally:
         solver.close()
     ue, ufe = w.meta["u"](xi).reshape(-1), w.meta["u"](xc).reshape(-1)
-    e_int = float(np.linalg.norm(u - ue) / np.linalg.norm(ue))
-    num = np.linalg.norm(u - ue) ** 2 + np.linalg.norm(uf - ufe) ** 2
     den = np.linalg.norm(ue) ** 2 + np.linalg.norm(ufe) ** 2
-    return {"leaves": L, "ppw": ppw, "kappa": kappa, "E_h": float(np.sqrt(num / den)), "E_h_interior": e_int,
-            "iterations": info["iterations"], "rel_residual": info["rel_residual"]}
+
+    def e_h(r):
+        return float(np.sqrt((np.linalg.norm(u[r] - ue) ** 2 + np.linalg.norm(uf[r] - ufe) ** 2) / den))
+
+    return {"kind": kind, "leaves": L, "p": p, "ppw": ppw, "kappa": kappa, "E_h": e_h(0), "E_h_it": e_h(1),
+            "E_h_interior": float(np.linalg.norm(u[0] - ue) / np.linalg.norm(ue)), "rprr": rprr,
+            "iterations": info1["iterations"], "iterations_rprr": info2["iterations"],
+            "rel_residual": info1["rel_residual"], "rel_residual_rprr": info2["rel_residual"]}
+
+
+def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
+    """Table PlaneMinErr entry (see accuracy_case)."""
+    return accuracy_case("plane", L=L, p=p, ppw=ppw, tol=tol)
 
 
 def large_solve(L=32, steps=3, warmup=1):
@@ -200,6 +220,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L", type=int, default=4)
     ap.add_argument("--ppw", type=float, nargs="*", default=[24.0, 19.2, 16.0, 12.0, 9.6])
+    ap.add_argument("--kind", nargs="*", default=["plane"], choices=["plane", "bumps"],
+                    help="exact solution of the accuracy runs: eq. (plane) and/or eq. (bumps)")
     ap.add_argument("--large", action="store_true", help="run the 32^3-leaf large solve instead")
     ap.add_argument("--multi-rhs", action="store_true", help="run the 64-RHS tensor-core workload instead")
     ap.add_argument("--sharing", action="store_true", help="run the shared-preconditioner-block sweep instead")
@@ -214,8 +236,9 @@ def main():
     if args.multi_rhs:
         print(json.dumps(multi_rhs(L=args.L if args.L != 4 else 16)), flush=True)
         return
-    for ppw in args.ppw:
-        print(json.dumps(plane_min_err(L=args.L, ppw=ppw)), flush=True)
+    for kind in args.kind:
+        for ppw in args.ppw:
+            print(json.dumps(accuracy_case(kind, L=args.L, ppw=ppw)), flush=True)
 
 
 if __name__ == "__main__":

@@ -1,10 +1,13 @@
-"""The paper's accuracy experiment (Sec. 6.2, Table PlaneMinErr) at n_c = 16 on
-4^3 leaves: E_h of the recovered solution over all N = N_l n leaf unknowns
-(interior and face nodes) against the printed value.  The mapping from points
-per wavelength to kappa is a reading of the tables of Sec. 6.1 (12 points per
-leaf and axis), so the printed values pin the order of magnitude only: within
-1.5 decades (E_h falls by ~6 decades over the printed range of ppw, so a wrong
-kappa by a factor 1.3 already moves it by about one decade)."""
+"""The paper's accuracy experiments (Sec. 6.2-6.3) at n_c = 16 on 4^3 leaves: E_h of
+the recovered solution over all N = N_l n leaf unknowns (interior and face nodes) for
+the plane-wave solution (Table PlaneMinErr) and the bumps solution (Table
+BumpsMinErr2), and E_h^it with the RPRR stopping rule (Table PlaneResRed).  The
+mapping from points per wavelength to kappa is a reading of the tables of Sec. 6.1
+(12 points per leaf and axis), so the printed values pin the order of magnitude
+only: within 1.5 decades (E_h falls by ~6 decades over the printed range of ppw, so
+a kappa off by a factor 1.3 already moves it by about one decade).  With the RPRR
+stopping rule the error stays within a decade of the converged one (the rule's
+purpose)."""
 
 import math
 import os
@@ -14,25 +17,35 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2112_02211_gb300.experiments import plane_min_err  # noqa: E402
+from paper_2112_02211_gb300.experiments import RPRR, accuracy_case  # noqa: E402
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_plane_min_err.txt")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _printed():
+def _printed(name, col=1):
     vals = {}
-    for line in open(GOLDEN):
+    for line in open(os.path.join(GOLDEN, name)):
         line = line.split("#", 1)[0].strip()
         if line:
-            a, b = line.split()
-            vals[float(a)] = float(b)
+            parts = line.split()
+            vals[float(parts[0])] = [float(v) for v in parts[1:]]
     return vals
 
 
-@pytest.mark.parametrize("ppw", [24.0, 9.6])
-def test_plane_min_err_order_of_magnitude(ppw):
-    printed = _printed()[ppw]
-    r = plane_min_err(L=4, p=16, ppw=ppw)
+def test_rprr_table_matches_golden():
+    for ppw, (rprr, _) in _printed("paper_plane_res_red.txt").items():
+        assert RPRR[ppw] == rprr
+
+
+@pytest.mark.parametrize("kind,ppw", [("plane", 24.0), ("bumps", 9.6)])
+def test_accuracy_tables_order_of_magnitude(kind, ppw):
+    table = "paper_plane_min_err.txt" if kind == "plane" else "paper_bumps_min_err.txt"
+    printed = _printed(table)[ppw][0]
+    r = accuracy_case(kind, L=4, p=16, ppw=ppw)
     print(r)
-    assert abs(math.log10(r["E_h"] / printed)) <= 1.5, r
     assert r["rel_residual"] < 1e-12
+    assert abs(math.log10(r["E_h"] / printed)) <= 1.5, r
+    assert r["E_h_it"] <= 10.0 * r["E_h"], r
+    if kind == "plane":
+        printed_it = _printed("paper_plane_res_red.txt")[ppw][1]
+        assert abs(math.log10(r["E_h_it"] / printed_it)) <= 1.5, r

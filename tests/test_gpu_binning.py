@@ -122,8 +122,8 @@ def tc_case():
 
 
 def test_shared_blocks_on_tensor_cores_match_oracle(tc_case):
-    """Complex-FP32 blocks through three TF32 products: the FP32 bar of the unshared
-    preconditioner; the same handle without the tensor cores agrees to FP32 rounding."""
+    """Complex-FP32 blocks through one TF32 product per term (both operands rounded to
+    10-bit mantissas): the FP16-block bar on the tensor-core path, the FP32 bar without it."""
     w, grid, M, b, t = tc_case
     rng = np.random.default_rng(17)
     r = (rng.standard_normal(grid.nf) + 1j * rng.standard_normal(grid.nf)).astype(np.complex64)
@@ -134,11 +134,11 @@ def test_shared_blocks_on_tensor_cores_match_oracle(tc_case):
         try:
             assert solver.precond_info() == (96, 2, len({(m,) for m in _masks(grid)}))
             z = solver.precond(torch.from_numpy(r).cuda()).cpu().numpy()
-            assert rel(z, ref) < 2e-5, tc
+            assert rel(z, ref) < (5e-3 if tc else 2e-5), tc
             out[tc] = z
         finally:
             solver.close()
-    assert rel(out[True], out[False]) < 1e-5
+    assert 0 < rel(out[True], out[False]) < 5e-3
 
 
 def test_solve_with_tensor_core_blocks(tc_case):

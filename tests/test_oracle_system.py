@@ -66,6 +66,20 @@ def test_manufactured_solution_converges():
         assert b_ < a / 10
 
 
+def test_bumps_solution_converges_spectrally():
+    """The bumps test solution of Sec. 6.3 (not separable) with the bump medium: the face
+    solution converges spectrally in p to its exact impedance data."""
+    errs = []
+    for p in (6, 8, 10):
+        w = W.manufactured_bumps(L=2, p=p, kappa=6.0)
+        grid, prob, rhs, (xi, xf, nrm, b, s, t) = _setup(w)
+        f = np.linalg.solve(O.dense_face_matrix(grid, prob.R), rhs)
+        errs.append(O.relative_error(f, w.exact_f[0](xf, nrm)))
+    assert errs[-1] < 1e-5
+    for a, b_ in zip(errs, errs[1:]):
+        assert b_ < a / 10
+
+
 def test_recovered_interior_solution_converges():
     """u = A^{-1}[s; P^{-1} f] from the face solution reproduces the manufactured u at
     the interior nodes, spectrally in p."""

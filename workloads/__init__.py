@@ -169,6 +169,51 @@ def manufactured(L=2, p=10, kappa=10.0, eta=None, tol=1e-12, with_bump=True):
                     s=[s], t=[imp], exact_f=[imp], tol=tol, meta={"u": u})
 
 
+def manufactured_bumps(L=2, p=10, kappa=10.0, eta=None, tol=1e-12, with_bump=True):
+    """u = (1 + e^{i kappa x})(1 + e^{i kappa y})(1 + e^{i kappa z}) ln(1 + x^2 + y^2 + z^2)
+    (Sec. 6.3, eq. (bumps), not separable) with s, t built from it; medium b of eq. (source)."""
+    eta = kappa if eta is None else eta
+    k = kappa
+    bfun = _paper_bump if with_bump else _zero
+
+    def parts(xyz):
+        xyz = np.asarray(xyz)
+        e = [np.exp(1j * k * xyz[..., a]) for a in range(3)]
+        f = [1.0 + ea for ea in e]
+        fp = [1j * k * ea for ea in e]
+        fpp = [-k * k * ea for ea in e]
+        r2 = np.sum(xyz * xyz, axis=-1)
+        g = np.log1p(r2)
+        gp = [2.0 * xyz[..., a] / (1.0 + r2) for a in range(3)]
+        lapg = (6.0 + 2.0 * r2) / (1.0 + r2) ** 2
+        return f, fp, fpp, g, gp, lapg
+
+    def u(xyz):
+        f, fp, fpp, g, gp, lapg = parts(xyz)
+        return f[0] * f[1] * f[2] * g
+
+    def grad(xyz):
+        f, fp, fpp, g, gp, lapg = parts(xyz)
+        F = f[0] * f[1] * f[2]
+        dF = [fp[0] * f[1] * f[2], f[0] * fp[1] * f[2], f[0] * f[1] * fp[2]]
+        return np.stack([dF[a] * g + F * gp[a] for a in range(3)], axis=-1)
+
+    def s(xyz):
+        f, fp, fpp, g, gp, lapg = parts(xyz)
+        F = f[0] * f[1] * f[2]
+        dF = [fp[0] * f[1] * f[2], f[0] * fp[1] * f[2], f[0] * f[1] * fp[2]]
+        lapF = fpp[0] * f[1] * f[2] + f[0] * fpp[1] * f[2] + f[0] * f[1] * fpp[2]
+        lap = lapF * g + 2.0 * sum(dF[a] * gp[a] for a in range(3)) + F * lapg
+        return -lap - k * k * (1.0 - bfun(xyz)) * F * g
+
+    def imp(xyz, n):
+        dn = np.sum(grad(xyz) * np.asarray(n), axis=-1)
+        return dn + 1j * eta * u(xyz)
+
+    return Workload(name="manufactured_bumps", nx=L, ny=L, nz=L, p=p, kappa=kappa, eta=eta, b=bfun,
+                    s=[s], t=[imp], exact_f=[imp], tol=tol, meta={"u": u})
+
+
 def plane_wave_4cubed():
     """Plain FP64 workload: 4^3 leaves, p = 8, q = 6, kappa = eta = 10, b = 0, s = 0."""
     w = plane_wave(L=4, p=8, kappa=10.0, eta=10.0, seed=1, tol=1e-10, name="plane_wave_4cubed")
