@@ -19,6 +19,9 @@ full_system     The paper's global system of Sec. 3 (eq. (2x2), Fig. 4) for
                 tiny grids: the cross-check that the face system is the same
                 discrete problem.
 kron            Lemma 1 and Algorithms 1 and 3 (Kronecker applies).
+full_iterative  The paper's iterative path on the global system: matrix-free
+                apply (Algorithms 1-2) and the per-leaf homogenized block-Jacobi
+                preconditioner of eq. (block_pc) (Algorithms 3-4).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
@@ -27,3 +30,4 @@ from .discretization import *  # noqa: F401,F403
 from .face_system import *  # noqa: F401,F403
 from .full_system import *  # noqa: F401,F403
 from .kron import *  # noqa: F401,F403
+from .full_iterative import *  # noqa: F401,F403
