@@ -108,6 +108,10 @@ typedef struct {
                          (leaves: one B block).  0 (default) keeps every lambda^tau; blocks are
                          still shared where values are bitwise equal.  Finite, >= 0.  Changes the
                          preconditioner only, never the converged solution. */
+  int full_system;    /* also build the paper's own iterative path on the global system
+                         (Sec. 3-4; hps_full_apply, hps_full_precond, hps_full_solve): per
+                         distinct homogenized constant the inverse Schur complement S~^{-1}, and
+                         the Algorithm 3 eigen-tables.  Default 0. */
 } hps_options;
 
 typedef struct {
@@ -238,6 +242,38 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
  */
 int hps_recover(hps_handle* h, const double* s, const double* f, int nrhs, double* u_out,
                 double* u_face_out, void* stream);
+
+/*
+ * The paper's own iterative path on the global system (Sec. 3-4), built with
+ * options.full_system.  Vectors hold u at every node of every leaf:
+ * [rhs][leaf][n] with n = n1^3 + 6 n1^2, the leaf's interior nodes (layout
+ * above) followed by its six faces' n1 x n1 Chebyshev nodes (face layout,
+ * hps_nodes' cheb_face_xyz).  Device pointers; p <= 14 for HPS_C128.
+ *
+ * hps_full_apply:   y = A u, A the global matrix of eq. (2x2): per leaf the
+ *                   collocated operator of eq. (leaf) (interior rows by 1D
+ *                   products along the three lines, Algorithm 1; face rows
+ *                   F = N + i eta I) plus the neighbour's outgoing rows
+ *                   G = N - i eta I across each shared face (Algorithm 2).
+ * hps_full_precond: z = blockdiag(A~^tau)^{-1} r, the per-leaf block-Jacobi
+ *                   preconditioner with homogenized leaf matrices (Sec. 4,
+ *                   eq. (block_pc), Algorithms 3 and 4): Algorithm 3 for
+ *                   A~_ii^{-1} and S~^{-1} = (A~^{-1})_bb per distinct (binned,
+ *                   options.lambda_bin) constant.
+ * hps_full_solve:   restarted GMRES on A u = [s; t; 0] with that preconditioner
+ *                   (right preconditioning; form HPS_FORM_FP64 or HPS_FORM_MIXED,
+ *                   optionally | HPS_SOLVE_NO_PRECOND), stopping on the FP64 true
+ *                   relative residual <= tol.  s: nrhs interior vectors or NULL;
+ *                   t: nrhs face vectors at Gauss points (moved to the Chebyshev
+ *                   face nodes by P^{-1}) or NULL; u_out: nrhs global vectors.
+ *                   Synchronous.  Errors as hps_gmres_solve.
+ * The face system above is the production path; this one is the paper's own
+ * design, kept for comparison.
+ */
+int hps_full_apply(hps_handle* h, int dtype, const void* u, void* y, int nrhs, void* stream);
+int hps_full_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream);
+int hps_full_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs, double tol, double* u_out,
+                   hps_solve_info* info, void* stream);
 
 /*
  * Distinct preconditioner blocks of the handle: clusters, distinct K_c blocks

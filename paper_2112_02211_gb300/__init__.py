@@ -70,7 +70,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, p, kappa, eta=None, b=None, forms=("fp64", "mixed"), restart=50,
                  cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0, precond_fp16=True, tc_apply=True,
-                 lean=False, lambda_bin=0.0):
+                 lean=False, lambda_bin=0.0, full_system=False):
         self.lib = N.load()
         self.nx, self.ny, self.nz, self.p, self.q = nx, ny, nz, p, p - 2
         self.nl = nx * ny * nz
@@ -94,6 +94,8 @@ class Solver:
         opt.tc_apply = 1 if tc_apply else 0
         opt.lean = 1 if lean else 0
         opt.lambda_bin = float(lambda_bin)
+        opt.full_system = 1 if full_system else 0
+        self.n = self.ni + self.nb  # global-system unknowns per leaf
         bb = None
         if b is not None:
             bb = np.ascontiguousarray(np.asarray(b, dtype=np.complex128).reshape(-1))
@@ -180,6 +182,39 @@ class Solver:
         uf = torch.empty(nrhs * self.nf, dtype=torch.complex128, device="cuda") if faces else None
         N.check(self.lib.hps_recover(self.handle, _ptr(s), _ptr(f), nrhs, _ptr(u), _ptr(uf), _stream(stream)))
         return (u, uf) if faces else u
+
+    # ---- the paper's iterative path on the global system (full_system=True) ----
+    def full_apply(self, u, out=None, stream=None):
+        """y = A u for the global system of Sec. 3.1 (device tensors, complex128 or complex64)."""
+        torch = _torch()
+        nrhs = u.numel() // (self.nl * self.n)
+        y = torch.empty_like(u) if out is None else out
+        dt = N.HPS_C128 if u.dtype == torch.complex128 else N.HPS_C64
+        N.check(self.lib.hps_full_apply(self.handle, dt, _ptr(u), _ptr(y), nrhs, _stream(stream)))
+        return y
+
+    def full_precond(self, r, out=None, stream=None):
+        """z = blockdiag(A~)^{-1} r, the per-leaf homogenized block-Jacobi of Sec. 4."""
+        torch = _torch()
+        nrhs = r.numel() // (self.nl * self.n)
+        z = torch.empty_like(r) if out is None else out
+        dt = N.HPS_C128 if r.dtype == torch.complex128 else N.HPS_C64
+        N.check(self.lib.hps_full_precond(self.handle, dt, _ptr(r), _ptr(z), nrhs, _stream(stream)))
+        return z
+
+    def full_solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=1, stream=None, precond=True):
+        """GMRES on the global system with the per-leaf block-Jacobi preconditioner; returns
+        (u, info) with u at every node of every leaf (device complex128)."""
+        torch = _torch()
+        u = torch.empty(nrhs * self.nl * self.n, dtype=torch.complex128, device="cuda")
+        info = N.SolveInfo()
+        f = _FORMS[form] | (0 if precond else N.HPS_SOLVE_NO_PRECOND)
+        rc = self.lib.hps_full_solve(self.handle, f, _ptr(s), _ptr(t), nrhs, float(tol), _ptr(u), ctypes.byref(info),
+                                     _stream(stream))
+        if rc not in (0, N.HPS_ENOCONV):
+            N.check(rc)
+        return u, {"iterations": info.iterations, "cycles": info.cycles, "converged": bool(info.converged),
+                   "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc}
 
     def precond_info(self):
         """(clusters, distinct K_c blocks, distinct B blocks) of the preconditioner."""

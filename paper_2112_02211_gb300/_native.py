@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
     _fields_ = [("forms", ctypes.c_int), ("restart", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("max_rhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
                 ("device", ctypes.c_int), ("precond_fp16", ctypes.c_int), ("tc_apply", ctypes.c_int),
-                ("lean", ctypes.c_int), ("lambda_bin", ctypes.c_double)]
+                ("lean", ctypes.c_int), ("lambda_bin", ctypes.c_double),
+                ("full_system", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -68,6 +69,10 @@ SIGNATURES = {
                                        ctypes.POINTER(SolveInfo), _P]),
     "hps_recover": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "hps_export": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "hps_full_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "hps_full_precond": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "hps_full_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P,
+                                      ctypes.POINTER(SolveInfo), _P]),
     "hps_precond_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
     "hps_memory_bytes": (ctypes.c_size_t, [_P]),

@@ -116,7 +116,7 @@ void free_handle(hps_handle* h) {
                   h->dct.int_mask, h->dct.b_off, h->dct.leaf_bcls, h->dct.bc_rep, h->dct.kc_off,
                   h->dct.kc_slot_begin, h->dct.kslot_class, h->dct.kc_members, h->dct.kitems[0], h->dct.kitems[1],
                   h->dct.kitems[2], h->dct.kitems[3], h->dct.cl_tpos, h->dct.lf_tpos, h->dct.brd, h->dct.bto,
-                  h->dct.bsc};
+                  h->dct.bsc, h->fs.d_cls, h->fs.Sinv64, h->fs.Sinv32, h->fs.eig};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -198,6 +198,7 @@ void hps_default_options(hps_options* o) {
   o->tc_apply = 1;
   o->lean = 0;
   o->lambda_bin = 0.0;
+  o->full_system = 0;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -322,6 +323,7 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
       if ((r = build_preconditioner(h, dc, st))) return r;
       if (fp16 && (r = build_precond_fp16(h, st))) return r;
     }
+    if (o.full_system && (r = build_full_system(h, dc, st))) return r;
     HPS_CUDA_TRY(cudaStreamSynchronize(st));
     return HPS_OK;
   };
@@ -376,6 +378,9 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
     tsize = ct.tsize;
   }
   bytes += (size_t)h.nint * c16 + sizeof(int);  // medium C kept for recovery, error word
+  if (o.full_system)  // S~^{-1} per leaf at most, class index, lambda values, Algorithm 3 tables
+    bytes += (size_t)h.nl * h.nb * h.nb * ((want64 && !o.lean ? c16 : 0) + (want32 ? c8 : 0)) +
+             (size_t)h.nl * (sizeof(int) + c16) + (size_t)3 * (2 * h.n1 * h.n1 + h.n1) * sizeof(double);
   // Krylov workspace of one solve (host inputs staged on the device)
   const int M1 = o.restart + 1;
   const size_t vb = (size_t)nrhs * h.nf * c16;
@@ -414,6 +419,98 @@ int hps_apply(hps_handle* h, int dtype, const void* f, void* y, int nrhs, void* 
     return HPS_EINVAL;
   }
   return HPS_OK;
+}
+
+int hps_full_apply(hps_handle* h, int dtype, const void* u, void* y, int nrhs, void* stream) {
+  if (!h || !u || !y || nrhs < 1 || u == y) {
+    set_error("hps_full_apply: bad arguments");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == HPS_C128) {
+    if (h->p > 14) {
+      set_error("hps_full_apply: complex-double global apply supports p <= 14");
+      return HPS_EINVAL;
+    }
+    HPS_CUDA_TRY(launch_full_apply(h, true, VType::C128, u, VType::C128, y, nullptr, nrhs, st));
+  } else if (dtype == HPS_C64) {
+    HPS_CUDA_TRY(launch_full_apply(h, false, VType::C64, u, VType::C64, y, nullptr, nrhs, st));
+  } else {
+    set_error("hps_full_apply: unknown dtype");
+    return HPS_EINVAL;
+  }
+  return HPS_OK;
+}
+
+int hps_full_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream) {
+  if (!h || !r || !z || nrhs < 1 || r == z) {
+    set_error("hps_full_precond: bad arguments");
+    return HPS_EINVAL;
+  }
+  if (!h->fs.built) {
+    set_error("hps_full_precond: the global-system path was not built (options.full_system)");
+    return HPS_EINVAL;
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == HPS_C128) {
+    if (!h->fs.Sinv64 || h->p > 14) {
+      set_error("hps_full_precond: complex-double blocks not built (HPS_FORM_FP64, p <= 14)");
+      return HPS_EINVAL;
+    }
+    HPS_CUDA_TRY(launch_full_precond(h, true, VType::C128, r, VType::C128, z, nrhs, st));
+  } else if (dtype == HPS_C64) {
+    if (!h->fs.Sinv32) {
+      set_error("hps_full_precond: complex-float blocks not built (HPS_FORM_MIXED)");
+      return HPS_EINVAL;
+    }
+    HPS_CUDA_TRY(launch_full_precond(h, false, VType::C64, r, VType::C64, z, nrhs, st));
+  } else {
+    set_error("hps_full_precond: unknown dtype");
+    return HPS_EINVAL;
+  }
+  return HPS_OK;
+}
+
+int hps_full_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs, double tol, double* u_out,
+                   hps_solve_info* info, void* stream) {
+  if (!h || !u_out || nrhs < 1 || !(tol > 0.0)) {
+    set_error("hps_full_solve: bad arguments");
+    return HPS_EINVAL;
+  }
+  const bool no_pc = (form & HPS_SOLVE_NO_PRECOND) != 0;
+  form &= ~HPS_SOLVE_NO_PRECOND;
+  if (form != HPS_FORM_FP64 && form != HPS_FORM_MIXED) {
+    set_error("hps_full_solve: form must be HPS_FORM_FP64 or HPS_FORM_MIXED");
+    return HPS_EINVAL;
+  }
+  if (!h->fs.built) {
+    set_error("hps_full_solve: the global-system path was not built (options.full_system)");
+    return HPS_EINVAL;
+  }
+  if (nrhs > h->opt.max_rhs || h->p > 14 || (form == HPS_FORM_FP64 && !h->fs.Sinv64) ||
+      (form == HPS_FORM_MIXED && !h->fs.Sinv32)) {
+    set_error("hps_full_solve: nrhs > max_rhs, p > 14, or the form's blocks were not built");
+    return HPS_EINVAL;
+  }
+  // device pointers only
+  for (const void* ptr : {(const void*)s, (const void*)t, (const void*)u_out}) {
+    if (!ptr) continue;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, ptr) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      set_error("hps_full_solve: s, t and u_out must be device pointers");
+      return HPS_EINVAL;
+    }
+  }
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  int rc = full_solve(h, form, !no_pc, (const double2*)s, (const double2*)t, nrhs, tol, (double2*)u_out, info, st);
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return rc;
 }
 
 int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream) {

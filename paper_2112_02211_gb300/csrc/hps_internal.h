@@ -7,6 +7,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -193,6 +194,19 @@ struct Profiler {
   }
 };
 
+// The paper's iterative path on the global system (Sec. 3-4): per distinct
+// (binned) homogenized constant S~^{-1} = (A~^{-1})_bb, row-major nb x nb, and
+// per axis the Algorithm 3 tables V (n1 x n1), V^{-1}, E (n1), row-major.
+struct FullSystem {
+  bool built = false;
+  int ncls = 0;
+  std::vector<int> cls;      // [nleaves] class of each leaf
+  int* d_cls = nullptr;
+  double2* Sinv64 = nullptr;
+  float2* Sinv32 = nullptr;
+  double* eig = nullptr;     // 3 x (2 n1^2 + n1)
+};
+
 struct KrylovSpace {
   int m = 0, nrhs = 0, nblk = 0;
   long long nf = 0;
@@ -244,6 +258,9 @@ struct hps_handle {
   double2* lambda_q = nullptr;  // nl: lambda^tau after binning (opt.lambda_bin), used by the preconditioner
   double2* cdiag = nullptr;   // nl x ni: C = kappa^2 (1 - b) at interior nodes (kept for recovery)
 
+  // the paper's global-system path (options.full_system)
+  hps::FullSystem fs;
+
   // preconditioner
   bool has_precond = false;
   hps::ClusterTables ct;
@@ -278,6 +295,9 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st);
 // (sizes in h->ct); uploads the cluster tables.  Before the block storage is
 // allocated.
 int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st);
+int compute_lambdas(hps_handle* h, const double2* cdiag, cudaStream_t st, std::vector<double2>& lamq);
+// S~^{-1} per distinct homogenized constant and the Algorithm 3 tables (full.cu uses them).
+int build_full_system(hps_handle* h, const double2* cdiag, cudaStream_t st);
 int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st);
 int build_precond_fp16(hps_handle* h, cudaStream_t st);
 int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, double2* uf,
@@ -315,9 +335,28 @@ cudaError_t launch_precond_tc(const hps_handle* h, const float2* t, float2* z, i
 cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType tin, const void* f, VType tout,
                         void* y, const double2* bvec, int nrhs, bool residual, cudaStream_t st);
 
+// ---- full.cu (the paper's global-system path) ----
+cudaError_t launch_full_apply(const hps_handle* h, bool fp64, VType tin, const void* u, VType tout, void* y,
+                              const double2* b, int nrhs, cudaStream_t st);
+cudaError_t launch_full_precond(const hps_handle* h, bool fp64, VType tin, const void* r, VType tout, void* z,
+                                int nrhs, cudaStream_t st);
+
 // ---- krylov.cu ----
-int krylov_alloc(hps_handle* h, int nrhs);
+int krylov_alloc(hps_handle* h, int nrhs, long long nvec = -1);
 void krylov_free(hps_handle* h);
+// Operators of one restarted GMRES: w = A z (inner precision), z = M^{-1} v,
+// and the FP64 residual r = b - A x, on vectors of length n per right-hand side.
+struct GmresOps {
+  long long n = 0;
+  bool pc = false;
+  std::function<cudaError_t(VType, const void*, VType, void*, int, cudaStream_t)> apply;
+  std::function<cudaError_t(VType, const void*, VType, void*, int, cudaStream_t)> precond;
+  std::function<cudaError_t(const double2*, const double2*, double2*, int, cudaStream_t)> residual;
+};
+int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b, double2* x, int nrhs, double tol,
+               hps_solve_info* info, cudaStream_t st);
+int full_solve(hps_handle* h, int form, bool use_precond, const double2* s, const double2* t, int nrhs, double tol,
+               double2* u, hps_solve_info* info, cudaStream_t st);
 int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol,
                 hps_solve_info* info, cudaStream_t st, bool use_precond);
 

@@ -18,6 +18,7 @@
 // block, warp shuffles, then a sequential sum over blocks), so results are
 // bitwise reproducible run to run.
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -576,17 +577,18 @@ struct Flt {};
 }  // namespace
 
 // ---------------------------------------------------------------------------
-int krylov_alloc(hps_handle* h, int nrhs) {
+int krylov_alloc(hps_handle* h, int nrhs, long long nvec) {
   KrylovSpace& k = h->ks;
   const int m = h->opt.restart;
-  if (k.V && k.nrhs >= nrhs && k.m == m) return HPS_OK;
+  if (nvec <= 0) nvec = h->nf;
+  if (k.V && k.nrhs >= nrhs && k.m == m && k.nf == nvec) return HPS_OK;
   krylov_free(h);
   k.m = m;
   k.nrhs = nrhs;
-  k.nf = h->nf;
-  k.nblk = (int)((h->nf + kChunk - 1) / kChunk);
+  k.nf = nvec;
+  k.nblk = (int)((nvec + kChunk - 1) / kChunk);
   const int M1 = m + 1;
-  const long long nf = h->nf;
+  const long long nf = nvec;
   size_t total = 0;
   auto alloc = [&](void** p, size_t bytes) -> int {
     bytes = std::max<size_t>(bytes, 16);
@@ -644,7 +646,7 @@ int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& ou
   const int nblk = 256;
   double* part = k.nrm;
   double* res = k.est + 3 * k.nrhs;
-  norm_partial_kernel<<<dim3(nblk, nrhs), 256, 0, st>>>(x, h->nf, nblk, part);
+  norm_partial_kernel<<<dim3(nblk, nrhs), 256, 0, st>>>(x, k.nf, nblk, part);
   HPS_CUDA_TRY(cudaGetLastError());
   norm_final_kernel<<<(nrhs + 63) / 64, 64, 0, st>>>(part, nblk, nrhs, res);
   HPS_CUDA_TRY(cudaGetLastError());
@@ -657,15 +659,14 @@ int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& ou
 
 }  // namespace
 
-int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol, hps_solve_info* info,
-                cudaStream_t st, bool use_precond) {
+int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b, double2* x, int nrhs, double tol,
+               hps_solve_info* info, cudaStream_t st) {
   const auto t0 = std::chrono::steady_clock::now();
-  const bool mixed = (form == HPS_FORM_MIXED);
-  int rc = krylov_alloc(h, nrhs);
+  int rc = krylov_alloc(h, nrhs, ops.n);
   if (rc) return rc;
   KrylovSpace& k = h->ks;
   const int m = k.m, M1 = m + 1;
-  const long long nf = h->nf;
+  const long long nf = ops.n;
   const size_t vb = (size_t)nrhs * nf * sizeof(double2);
   double* est = k.est;
   double* invn = k.est + nrhs;
@@ -687,7 +688,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
   std::vector<double> htarget(nrhs), hinv(nrhs);
   std::vector<int> hact(nrhs);
   bool converged = false;
-  const bool pc = h->has_precond && use_precond;
+  const bool pc = ops.pc;
   while (true) {
     bool all = true;
     for (int r = 0; r < nrhs; ++r)
@@ -726,20 +727,12 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
       double2* vj = k.V + (long long)j * nrhs * nf;
       double2* w = k.V + (long long)(j + 1) * nrhs * nf;
       // z = M^{-1} v_j ; w = A z
-      if (mixed) {
-        if (pc) {
-          HPS_CUDA_TRY(launch_precond(h, true, VType::DF, vj, VType::C64, k.z, k.zt, nrhs, st, h->Kc16 != nullptr));
-          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::C64, k.z, VType::DF, w, nullptr, nrhs, false, st));
-        } else {
-          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, true, VType::DF, vj, VType::DF, w, nullptr, nrhs, false, st));
-        }
+      const VType vt = mixed ? VType::DF : VType::C128, zt = mixed ? VType::C64 : VType::C128;
+      if (pc) {
+        HPS_CUDA_TRY(ops.precond(vt, vj, zt, k.z, nrhs, st));
+        HPS_CUDA_TRY(ops.apply(zt, k.z, vt, w, nrhs, st));
       } else {
-        if (pc) {
-          HPS_CUDA_TRY(launch_precond(h, false, VType::C128, vj, VType::C128, k.z, k.zt, nrhs, st));
-          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, false, VType::C128, k.z, VType::C128, w, nullptr, nrhs, false, st));
-        } else {
-          HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_APPLY, false, VType::C128, vj, VType::C128, w, nullptr, nrhs, false, st));
-        }
+        HPS_CUDA_TRY(ops.apply(vt, vj, vt, w, nrhs, st));
       }
       VecArgs va;
       va.V = k.V;
@@ -826,10 +819,10 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     const long long nall = (long long)nrhs * nf;
     if (pc) {
       if (mixed) {
-        HPS_CUDA_TRY(launch_precond(h, true, VType::C128, k.u, VType::C64, k.z, k.zt, nrhs, st, h->Kc16 != nullptr));
+        HPS_CUDA_TRY(ops.precond(VType::C128, k.u, VType::C64, k.z, nrhs, st));
         xpy_kernel<float2><<<4 * h->nsm, 256, 0, st>>>(x, (const float2*)k.z, nall);
       } else {
-        HPS_CUDA_TRY(launch_precond(h, false, VType::C128, k.u, VType::C128, k.z, k.zt, nrhs, st));
+        HPS_CUDA_TRY(ops.precond(VType::C128, k.u, VType::C128, k.z, nrhs, st));
         xpy_kernel<double2><<<4 * h->nsm, 256, 0, st>>>(x, (const double2*)k.z, nall);
       }
     } else {
@@ -838,10 +831,8 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     HPS_CUDA_TRY(cudaGetLastError());
     h->prof.end(HPS_PHASE_UPDATE, ev_up, st);
     h->prof.launches += 3;
-    // true residual with the FP64 maps
-    // FP64 maps, or in lean mode the FP32 maps against FP64 vectors
-    HPS_CUDA_TRY(timed_apply(h, HPS_PHASE_RESIDUAL, h->R64 == nullptr, VType::C128, x, VType::C128, k.r, b, nrhs,
-                             true, st));
+    // true residual r = b - A x in FP64
+    HPS_CUDA_TRY(ops.residual(x, b, k.r, nrhs, st));
     if ((rc = vec_norms(h, k.r, nrhs, rnorm, st))) return rc;
     if (h->tc_error) {
       int terr = 0;
@@ -868,6 +859,27 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     return HPS_ENOCONV;
   }
   return HPS_OK;
+}
+
+// GMRES on the face system (I + Pi R) f = b: apply and preconditioner of
+// apply.cu; FP64 residual with the FP64 maps (in lean mode the FP32 maps
+// against FP64 vectors).
+int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol, hps_solve_info* info,
+                cudaStream_t st, bool use_precond) {
+  const bool mixed = (form == HPS_FORM_MIXED);
+  GmresOps ops;
+  ops.n = h->nf;
+  ops.pc = h->has_precond && use_precond;
+  ops.apply = [h, mixed](VType tin, const void* in, VType tout, void* out, int nrhs, cudaStream_t s) {
+    return timed_apply(h, HPS_PHASE_APPLY, mixed, tin, in, tout, out, nullptr, nrhs, false, s);
+  };
+  ops.precond = [h, mixed](VType tin, const void* in, VType tout, void* out, int nrhs, cudaStream_t s) {
+    return launch_precond(h, mixed, tin, in, tout, out, h->ks.zt, nrhs, s, mixed && h->Kc16 != nullptr);
+  };
+  ops.residual = [h](const double2* xx, const double2* bb, double2* r, int nrhs, cudaStream_t s) {
+    return timed_apply(h, HPS_PHASE_RESIDUAL, h->R64 == nullptr, VType::C128, xx, VType::C128, r, bb, nrhs, true, s);
+  };
+  return gmres_core(h, ops, mixed, b, x, nrhs, tol, info, st);
 }
 
 }  // namespace hps

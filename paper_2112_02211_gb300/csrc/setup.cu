@@ -1216,9 +1216,16 @@ int upload(hps_handle* h, V*& dst, const std::vector<V>& vec, cudaStream_t st) {
 }
 }  // namespace
 
-int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
-  ClusterTables& ct = h->ct;
-  int rc;
+// lambda^tau of every leaf (h->lambda) and its binned value (h->lambda_q); the
+// binned values are returned on the host.  Computed once per handle.
+int compute_lambdas(hps_handle* h, const double2* cdiag, cudaStream_t st, std::vector<double2>& lamq) {
+  lamq.assign(h->nl, make_double2(0.0, 0.0));
+  if (h->lambda_q) {
+    HPS_CUDA_TRY(cudaMemcpyAsync(lamq.data(), h->lambda_q, (size_t)h->nl * sizeof(double2), cudaMemcpyDeviceToHost,
+                                 st));
+    HPS_CUDA_TRY(cudaStreamSynchronize(st));
+    return HPS_OK;
+  }
   HPS_CUDA_TRY(cudaMalloc(&h->lambda_q, (size_t)h->nl * sizeof(double2)));
   h->bytes += (size_t)h->nl * sizeof(double2);
   lambda_kernel<<<h->nl, 256, 0, st>>>(cdiag, h->ni, h->lambda);
@@ -1233,10 +1240,19 @@ int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st
     for (const double2& l : lam) mx = std::max(mx, std::hypot(l.x, l.y));
     w = h->opt.lambda_bin * mx;
   }
-  std::vector<double2> lamq(lam);
+  lamq = lam;
   if (w > 0.0)
     for (double2& l : lamq) l = make_double2(w * std::nearbyint(l.x / w), w * std::nearbyint(l.y / w));
   HPS_CUDA_TRY(cudaMemcpyAsync(h->lambda_q, lamq.data(), (size_t)h->nl * sizeof(double2), cudaMemcpyHostToDevice, st));
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  return HPS_OK;
+}
+
+int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+  ClusterTables& ct = h->ct;
+  int rc;
+  std::vector<double2> lamq;
+  if ((rc = compute_lambdas(h, cdiag, st, lamq))) return rc;
   assign_blocks(h, &lamq);
   if ((rc = upload(h, h->dct.slot_lf, ct.slot_lf, st))) return rc;
   if ((rc = upload(h, h->dct.slot_cluster, ct.slot_cluster, st))) return rc;
@@ -1290,6 +1306,271 @@ int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st) {
   if (d_leaves) cudaFree(d_leaves);
   if (d_slot_lf) cudaFree(d_slot_lf);
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// The paper's own iterative path on the global system (Sec. 3-4): per distinct
+// homogenized constant, S~^{-1} = (A~^{-1})_bb (the inverse of the Schur
+// complement F_bb - F_bi A~_ii^{-1} A_ib of eq. (block_pc) is the boundary
+// block of the inverse of the homogenized leaf matrix), and per axis the
+// eigen-decomposition L1 = V E V^{-1} of Algorithm 3.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void extract_sinv_kernel(const double2* W, long long wstride, int ld, int n, int ni, int nb, int nbatch,
+                                    const int* cls, double2* S64, float2* S32) {
+  const int b = blockIdx.y;
+  if (b >= nbatch) return;
+  const long long off = (long long)cls[b] * nb * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nb * nb;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / nb), c = (int)(t % nb);
+    const double2 v = W[(long long)b * wstride + (long long)(ni + r) * ld + n + c];
+    if (S64) S64[off + t] = v;
+    if (S32) S32[off + t] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// Real eigen-decomposition M = V diag(E) V^{-1} of a small matrix with real,
+// distinct eigenvalues (the interior block of the squared Chebyshev
+// differentiation matrix): QR iteration with the last diagonal entry as shift
+// and deflation, then inverse iteration for each eigenvector and Gauss-Jordan
+// for V^{-1}.  Returns false when it does not converge or does not reproduce M.
+bool small_eig(int n, const std::vector<double>& M, std::vector<double>& V, std::vector<double>& Vi,
+               std::vector<double>& E) {
+  auto at = [n](std::vector<double>& A, int i, int j) -> double& { return A[(size_t)i * n + j]; };
+  std::vector<double> T(M);
+  double nrm = 0.0;
+  for (double v : M) nrm = std::max(nrm, std::fabs(v));
+  if (nrm == 0.0) return false;
+  E.assign(n, 0.0);
+  int m = n;
+  struct Rot {
+    double c, s;
+    int i0, i1;
+  };
+  for (int iter = 0; m > 0 && iter < 100000; ++iter) {
+    if (m == 1) {
+      E[0] = at(T, 0, 0);
+      m = 0;
+      break;
+    }
+    double last = 0.0;
+    for (int j = 0; j + 1 < m; ++j) last = std::max(last, std::fabs(at(T, m - 1, j)));
+    if (last <= 1e-15 * nrm) {
+      E[m - 1] = at(T, m - 1, m - 1);
+      --m;
+      continue;
+    }
+    const double mu = at(T, m - 1, m - 1);
+    for (int i = 0; i < m; ++i) at(T, i, i) -= mu;
+    // QR of the leading m x m block by Givens rotations (T <- Q^T T = R), then T <- R Q
+    std::vector<Rot> rots;
+    for (int k = 0; k + 1 < m; ++k) {
+      for (int i = m - 1; i > k; --i) {
+        const double a = at(T, i - 1, k), b = at(T, i, k);
+        if (b == 0.0) continue;
+        const double r = std::hypot(a, b), cc = a / r, ss = b / r;
+        for (int j = 0; j < m; ++j) {
+          const double x = at(T, i - 1, j), y = at(T, i, j);
+          at(T, i - 1, j) = cc * x + ss * y;
+          at(T, i, j) = -ss * x + cc * y;
+        }
+        rots.push_back({cc, ss, i - 1, i});
+      }
+    }
+    for (const Rot& g : rots)
+      for (int row = 0; row < m; ++row) {
+        const double x = at(T, row, g.i0), y = at(T, row, g.i1);
+        at(T, row, g.i0) = g.c * x + g.s * y;
+        at(T, row, g.i1) = -g.s * x + g.c * y;
+      }
+    for (int i = 0; i < m; ++i) at(T, i, i) += mu;
+  }
+  if (m != 0) return false;
+  // eigenvectors by inverse iteration
+  V.assign((size_t)n * n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const double shift = E[k] + 1e-10 * nrm;
+    std::vector<double> x(n);
+    for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.1 * i;
+    for (int it = 0; it < 4; ++it) {
+      // solve (M - shift I) y = x by Gaussian elimination with partial pivoting
+      std::vector<double> A(M);
+      for (int i = 0; i < n; ++i) at(A, i, i) -= shift;
+      std::vector<double> y(x);
+      for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+          if (std::fabs(at(A, r, col)) > std::fabs(at(A, piv, col))) piv = r;
+        if (at(A, piv, col) == 0.0) return false;
+        if (piv != col) {
+          for (int j = 0; j < n; ++j) std::swap(at(A, col, j), at(A, piv, j));
+          std::swap(y[col], y[piv]);
+        }
+        for (int r = col + 1; r < n; ++r) {
+          const double f = at(A, r, col) / at(A, col, col);
+          if (f == 0.0) continue;
+          for (int j = col; j < n; ++j) at(A, r, j) -= f * at(A, col, j);
+          y[r] -= f * y[col];
+        }
+      }
+      for (int r = n - 1; r >= 0; --r) {
+        double v = y[r];
+        for (int j = r + 1; j < n; ++j) v -= at(A, r, j) * y[j];
+        y[r] = v / at(A, r, r);
+      }
+      double yn = 0.0;
+      for (double v : y) yn += v * v;
+      yn = std::sqrt(yn);
+      if (!(yn > 0.0) || !std::isfinite(yn)) return false;
+      for (int i = 0; i < n; ++i) x[i] = y[i] / yn;
+    }
+    for (int i = 0; i < n; ++i) at(V, i, k) = x[i];
+  }
+  // V^{-1} by Gauss-Jordan with partial pivoting
+  std::vector<double> A(V);
+  Vi.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) at(Vi, i, i) = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(at(A, r, col)) > std::fabs(at(A, piv, col))) piv = r;
+    if (at(A, piv, col) == 0.0) return false;
+    for (int j = 0; j < n; ++j) {
+      std::swap(at(A, col, j), at(A, piv, j));
+      std::swap(at(Vi, col, j), at(Vi, piv, j));
+    }
+    const double d = at(A, col, col);
+    for (int j = 0; j < n; ++j) {
+      at(A, col, j) /= d;
+      at(Vi, col, j) /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = at(A, r, col);
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        at(A, r, j) -= f * at(A, col, j);
+        at(Vi, r, j) -= f * at(Vi, col, j);
+      }
+    }
+  }
+  // check M V = V E and V V^{-1} = I
+  double err = 0.0, err2 = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      double mv = 0.0, vvi = 0.0;
+      for (int j = 0; j < n; ++j) {
+        mv += M[(size_t)i * n + j] * V[(size_t)j * n + k];
+        vvi += V[(size_t)i * n + j] * Vi[(size_t)j * n + k];
+      }
+      err = std::max(err, std::fabs(mv - V[(size_t)i * n + k] * E[k]));
+      err2 = std::max(err2, std::fabs(vvi - (i == k ? 1.0 : 0.0)));
+    }
+  return err <= 1e-9 * nrm && err2 <= 1e-9;
+}
+
+}  // namespace
+
+int build_full_system(hps_handle* h, const double2* cdiag, cudaStream_t st) {
+  FullSystem& fs = h->fs;
+  const int n = h->n, ni = h->ni, nb = h->nb, n1 = h->n1, p = h->p;
+  int rc = HPS_OK;
+  std::vector<double2> lamq;
+  if ((rc = compute_lambdas(h, cdiag, st, lamq))) return rc;
+  // distinct homogenized constants
+  std::map<std::pair<uint64_t, uint64_t>, int> keys;
+  fs.cls.assign(h->nl, 0);
+  std::vector<int> rep;
+  for (int leaf = 0; leaf < h->nl; ++leaf) {
+    double re = lamq[leaf].x + 0.0, im = lamq[leaf].y + 0.0;
+    uint64_t a, b;
+    std::memcpy(&a, &re, 8);
+    std::memcpy(&b, &im, 8);
+    auto it = keys.find({a, b});
+    if (it == keys.end()) {
+      it = keys.emplace(std::make_pair(a, b), (int)rep.size()).first;
+      rep.push_back(leaf);
+    }
+    fs.cls[leaf] = it->second;
+  }
+  fs.ncls = (int)rep.size();
+  const bool want64 = (h->opt.forms & HPS_FORM_FP64) != 0, want32 = (h->opt.forms & HPS_FORM_MIXED) != 0;
+  const size_t per = (size_t)nb * nb;
+  auto dal = [&](void** ptr, size_t bytes) -> int {
+    HPS_CUDA_TRY(cudaMalloc(ptr, std::max<size_t>(bytes, 16)));
+    h->bytes += std::max<size_t>(bytes, 16);
+    return HPS_OK;
+  };
+  if (want64 && !h->opt.lean && (rc = dal((void**)&fs.Sinv64, per * fs.ncls * sizeof(double2)))) return rc;
+  if (want32 && (rc = dal((void**)&fs.Sinv32, per * fs.ncls * sizeof(float2)))) return rc;
+  if ((rc = dal((void**)&fs.d_cls, (size_t)h->nl * sizeof(int)))) return rc;
+  HPS_CUDA_TRY(cudaMemcpyAsync(fs.d_cls, fs.cls.data(), (size_t)h->nl * sizeof(int), cudaMemcpyHostToDevice, st));
+  // S~^{-1} of every distinct constant from the elimination of its homogenized leaf matrix
+  {
+    const int ncols = n + nb, ld = ncols;
+    const long long wstride = (long long)n * ld;
+    const size_t perw = (size_t)wstride * sizeof(double2);
+    int nbatch = (int)std::min<size_t>((size_t)fs.ncls, std::max<size_t>(1, workspace_budget(h) / perw));
+    nbatch = std::min(nbatch, 4 * h->nsm);
+    double2* W = nullptr;
+    int *d_status = nullptr, *d_leaves = nullptr, *d_seq = nullptr;
+    HPS_CUDA_TRY(cudaMalloc(&W, perw * nbatch));
+    HPS_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
+    HPS_CUDA_TRY(cudaMalloc(&d_leaves, (size_t)fs.ncls * sizeof(int)));
+    HPS_CUDA_TRY(cudaMalloc(&d_seq, (size_t)fs.ncls * sizeof(int)));
+    std::vector<int> seq(fs.ncls);
+    for (int k = 0; k < fs.ncls; ++k) seq[k] = k;
+    HPS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+    HPS_CUDA_TRY(cudaMemcpyAsync(d_leaves, rep.data(), (size_t)fs.ncls * sizeof(int), cudaMemcpyHostToDevice, st));
+    HPS_CUDA_TRY(cudaMemcpyAsync(d_seq, seq.data(), (size_t)fs.ncls * sizeof(int), cudaMemcpyHostToDevice, st));
+    for (int k0 = 0; k0 < fs.ncls && rc == HPS_OK; k0 += nbatch) {
+      const int nbt = std::min(nbatch, fs.ncls - k0);
+      auto body = [&]() -> int {
+        HPS_CUDA_TRY(cudaMemsetAsync(W, 0, perw * nbt, st));
+        assemble_kernel<double2><<<dim3((n + 127) / 128, nbt), 128, 0, st>>>(
+            W, wstride, ld, d_leaves + k0, 0, nbt, h->tables, h->tl, h->eta, nullptr, h->lambda_q, 1);
+        HPS_CUDA_TRY(cudaGetLastError());
+        HPS_CUDA_TRY(run_gj(W, wstride, ld, n, ncols, ni, nbt, d_status, st));
+        extract_sinv_kernel<<<dim3(64, nbt), 256, 0, st>>>(W, wstride, ld, n, ni, nb, nbt, d_seq + k0, fs.Sinv64,
+                                                          fs.Sinv32);
+        HPS_CUDA_TRY(cudaGetLastError());
+        return HPS_OK;
+      };
+      rc = body();
+    }
+    if (rc == HPS_OK) rc = check_status(d_status, st, "homogenized leaf systems");
+    cudaStreamSynchronize(st);
+    cudaFree(W);
+    cudaFree(d_status);
+    cudaFree(d_leaves);
+    cudaFree(d_seq);
+    if (rc) return rc;
+  }
+  // Algorithm 3 tables: L1 = (D~^2)[1..p-2][1..p-2] = V E V^{-1} per axis
+  std::vector<double> tab(h->tl.total);
+  HPS_CUDA_TRY(cudaMemcpyAsync(tab.data(), h->tables, tab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  const size_t pa = (size_t)2 * n1 * n1 + n1;
+  std::vector<double> eig(3 * pa);
+  for (int axis = 0; axis < 3; ++axis) {
+    std::vector<double> M((size_t)n1 * n1), V, Vi, E;
+    for (int i = 0; i < n1; ++i)
+      for (int j = 0; j < n1; ++j) M[(size_t)i * n1 + j] = tab[h->tl.D2 + (size_t)axis * p * p + (i + 1) * p + (j + 1)];
+    if (!small_eig(n1, M, V, Vi, E)) {
+      set_error("eigen-decomposition of the 1D second-derivative block failed");
+      return HPS_EBREAKDOWN;
+    }
+    std::copy(V.begin(), V.end(), eig.begin() + axis * pa);
+    std::copy(Vi.begin(), Vi.end(), eig.begin() + axis * pa + (size_t)n1 * n1);
+    std::copy(E.begin(), E.end(), eig.begin() + axis * pa + (size_t)2 * n1 * n1);
+  }
+  if ((rc = dal((void**)&fs.eig, eig.size() * sizeof(double)))) return rc;
+  HPS_CUDA_TRY(cudaMemcpyAsync(fs.eig, eig.data(), eig.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  HPS_CUDA_TRY(cudaStreamSynchronize(st));
+  fs.built = true;
+  return HPS_OK;
 }
 
 }  // namespace hps
