@@ -356,7 +356,7 @@ def run_gpu(args, dist):
     kernels = {"apply": "seg_gemv_kernel<ApplyP<float2,float2,float4>,1,4>",
                "precond_k": "tc_precond_kernel (blocks shared by >= 16 clusters) + "
                             "seg_gemv_kernel<PrecKP<__half2,float2,float2>,W,R> (W = 1, 2, 4, 8 clusters per block)",
-               "precond_b": "seg_gemv_kernel<PrecBP<__half2,float4,float2>,1,4>"}
+               "precond_b": "prec_b_kernel<__half2,float4,float2> (one thread per row, B transposed)"}
     roof = {}
     for ph, by in phases.items():
         cnt = prof["count"][ph]

@@ -709,10 +709,24 @@ long long hps_export(hps_handle* h, int what, int index, double* host_out) {
     case HPS_EXPORT_B: {
       if (!h->has_precond || index < 0 || index >= h->nl) break;
       const int ni_ = __builtin_popcount(h->ct.int_mask[index]);
-      const int rows = ni_ * q2, cols = (6 - ni_) * q2, ld = (int)rup4(cols);
+      const int rows = ni_ * q2, cols = (6 - ni_) * q2, ldr = (int)rup4(rows);
       if (rows == 0) return 0;
-      if (h->B64) return copy2d(h->B64 + h->ct.b_off[index], sizeof(double2), rows, cols, ld, false);
-      return copy2d(h->B32 + h->ct.b_off[index], sizeof(float2), rows, cols, ld, true);
+      // stored transposed (column c holds the rows): copy cols x rows, return rows x cols
+      const long long count = 2LL * rows * cols;
+      if (!host_out) return count;
+      std::vector<double> tmp((size_t)count);
+      double* keep = host_out;
+      host_out = tmp.data();
+      const long long rc2 = h->B64 ? copy2d(h->B64 + h->ct.b_off[index], sizeof(double2), cols, rows, ldr, false)
+                                   : copy2d(h->B32 + h->ct.b_off[index], sizeof(float2), cols, rows, ldr, true);
+      host_out = keep;
+      if (rc2 < 0) return rc2;
+      for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) {
+          host_out[2 * ((size_t)r * cols + c)] = tmp[2 * ((size_t)c * rows + r)];
+          host_out[2 * ((size_t)r * cols + c) + 1] = tmp[2 * ((size_t)c * rows + r) + 1];
+        }
+      return count;
     }
     default:
       break;

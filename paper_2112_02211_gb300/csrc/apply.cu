@@ -5,7 +5,8 @@
 //  * residual  y = b - (f + Pi (R f))
 //  * rhs       b = tbar - Pi (H s)        (body-load response of each leaf)
 //  * precond   z = J^{-1} r on 2x2x2 clusters (Sec. 4, Algorithm 4 in face form):
-//      stage B  z_ext = r_ext,  t = r_int - B r_ext   (B = internal rows of R~)
+//      stage B  z_ext = r_ext,  t = r_int - B r_ext   (B = internal rows of R~;
+//               its own kernel, one thread per row, B stored transposed)
 //      stage K  z_int = K_c t                          (K_c = (I + D)^{-1})
 //
 // An item is (leaf, face) for apply/rhs (rows of that face's block), a leaf
@@ -209,68 +210,6 @@ struct RhsP {
   }
 };
 
-template <class TM_, class TIN, class TOUT>
-struct PrecBP {
-  using TM = TM_;
-  using Acc = typename MT<TM>::Acc;
-  struct Args {
-    const TM* B;
-    const float* bscale;  // FP16 blocks: row scales, index bsc[leaf*6 + k] + j
-    const long long* b_off;
-    const uint8_t* int_mask;
-    const int* brd;  // per leaf, internal faces then external: input offsets
-    const int* bto;  // per leaf, internal faces: t offsets
-    const int* bsc;  // per leaf, internal faces: row-scale bases
-    int nb, q2;
-    const TIN* r;
-    TOUT* z;
-    TOUT* t;
-    long long nf, tstride;
-    int nrhs;
-    long long nitems;
-  };
-  // One item per leaf: the rows of all its internal faces (B^leaf) against the
-  // values on its external faces, plus the copy of the external faces.  The
-  // offsets of the faces involved come from per-leaf tables.
-  __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
-    it.leaf = (int)item;
-    const int nint = __popc((unsigned)A.int_mask[it.leaf]);
-    it.mask = nint;
-    if (nint == 0) return false;
-    it.nrows = nint * A.q2;
-    it.ncols = (6 - nint) * A.q2;
-    it.ld = (int)rup4(it.ncols);
-    it.mat = A.B + A.b_off[it.leaf];
-    return true;
-  }
-  __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rhs, int c) {
-    const int k = c / A.q2;
-    return cvt<Acc>(A.r[rhs * A.nf + A.brd[it.leaf * 6 + it.mask + k] + (c - k * A.q2)]);
-  }
-  __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int nr, int tid) {
-    for (int idx = tid; idx < nr * it.nrows; idx += kThreads) {
-      const int rhs = idx / it.nrows, row = idx % it.nrows;
-      const int k = row / A.q2, j = row - k * A.q2;
-      const int e = it.leaf * 6 + k;
-      const Acc g = rscale(outs[idx], A.bscale, (long long)A.bsc[e] + j);
-      const Acc v = csub(cvt<Acc>(A.r[rhs * A.nf + A.brd[e] + j]), g);
-      A.t[rhs * A.tstride + A.bto[e] + j] = cvt<TOUT>(v);
-    }
-    copy(A, it, nr, tid);
-  }
-  // z = r on the faces leaving the leaf's cluster
-  __device__ static void copy(const Args& A, const ItemInfo& it, int nr, int tid) {
-    const int nint = __popc((unsigned)A.int_mask[it.leaf]);
-    const int n = (6 - nint) * A.q2;
-    for (int idx = tid; idx < nr * n; idx += kThreads) {
-      const int rhs = idx / n, e = idx % n;
-      const int k = e / A.q2;
-      const long long o = rhs * A.nf + A.brd[it.leaf * 6 + nint + k] + (e - k * A.q2);
-      A.z[o] = cvt<TOUT>(cvt<Acc>(A.r[o]));
-    }
-  }
-};
-
 // Stage K over distinct blocks: item = (block k, block slot s, first member,
 // member count) with the members the clusters sharing block k; "right-hand
 // side" rr of the item is member rr (one right-hand side per launch).
@@ -402,6 +341,65 @@ __global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Ar
   }
 }
 
+// Stage B: one CTA per leaf (persistent), one thread per row of the leaf's B
+// block.  B is stored transposed (column c holds the nint q^2 rows), so a warp
+// reads 32 consecutive rows of one column: coalesced loads and no cross-lane
+// reductions.  The external-face values are staged in shared memory; t at the
+// neighbours' internal slots gets r - B r_ext, z_ext = r_ext.
+template <class TM, class TIN, class TOUT>
+struct PrecBArgs {
+  const TM* B;
+  const float* bscale;  // FP16 blocks: row scales, index bsc[leaf*6 + k] + j
+  const long long* b_off;
+  const uint8_t* int_mask;
+  const int* brd;  // per leaf, internal faces then external: input offsets
+  const int* bto;  // per leaf, internal faces: t offsets
+  const int* bsc;  // per leaf, internal faces: row-scale bases
+  int nl, q2;
+  const TIN* r;
+  TOUT* z;
+  TOUT* t;
+};
+
+template <class TM> __device__ __forceinline__ typename MT<TM>::Acc load_one(const TM* p);
+template <> __device__ __forceinline__ float2 load_one<__half2>(const __half2* p) { return __half22float2(*p); }
+template <> __device__ __forceinline__ float2 load_one<float2>(const float2* p) { return *p; }
+template <> __device__ __forceinline__ double2 load_one<double2>(const double2* p) { return *p; }
+
+template <class TM, class TIN, class TOUT>
+__global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TIN, TOUT> A) {
+  using Acc = typename MT<TM>::Acc;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Acc* xs = reinterpret_cast<Acc*>(smraw);  // 6 q^2
+  const int q2 = A.q2;
+  for (int leaf = blockIdx.x; leaf < A.nl; leaf += gridDim.x) {
+    const int nint = __popc((unsigned)A.int_mask[leaf]);
+    const int ncols = (6 - nint) * q2, nrows = nint * q2;
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncols; c += kThreads) {
+      const int k = c / q2;
+      const long long o = A.brd[leaf * 6 + nint + k] + (c - k * q2);
+      const Acc v = cvt<Acc>(A.r[o]);
+      xs[c] = v;
+      A.z[o] = cvt<TOUT>(v);
+    }
+    __syncthreads();
+    if (nint == 0) continue;
+    const TM* Bm = A.B + A.b_off[leaf];
+    const int ldr = (int)rup4(nrows);
+    for (int row = threadIdx.x; row < nrows; row += kThreads) {
+      Acc acc = czero<Acc>();
+#pragma unroll 4
+      for (int c = 0; c < ncols; ++c) cfma(acc, load_one<TM>(Bm + (long long)c * ldr + row), xs[c]);
+      const int k = row / q2, j = row - k * q2;
+      const int e = leaf * 6 + k;
+      const Acc g = rscale(acc, A.bscale, (long long)A.bsc[e] + j);
+      const Acc v = csub(cvt<Acc>(A.r[A.brd[e] + j]), g);
+      A.t[A.bto[e] + j] = cvt<TOUT>(v);
+    }
+  }
+}
+
 template <class P, int NR, int RPW>
 cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm, cudaStream_t st, long long* counter) {
   using Acc = typename P::Acc;
@@ -479,8 +477,7 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
   const int q2 = h->q * h->q;
   const long long tstride = h->ct.tsize;
   {
-    using P = PrecBP<TM, TIN, TOUT>;
-    typename P::Args A;
+    PrecBArgs<TM, TIN, TOUT> A;
     A.B = B;
     A.bscale = bscale;
     A.b_off = h->dct.b_off;
@@ -488,21 +485,24 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.brd = h->dct.brd;
     A.bto = h->dct.bto;
     A.bsc = h->dct.bsc;
-    A.nb = h->nb;
+    A.nl = h->nl;
     A.q2 = q2;
-    A.r = r;
-    A.z = z;
-    A.t = t;
-    A.nf = h->nf;
-    A.tstride = tstride;
-    A.nrhs = nrhs;
-    A.nitems = (long long)h->nl;
+    using Acc = typename MT<TM>::Acc;
+    const size_t smem = (size_t)h->nb * sizeof(Acc);
+    auto kern = prec_b_kernel<TM, TIN, TOUT>;
     cudaEvent_t ev = h->prof.begin(st);
-    cudaError_t e = launch_groups<P>(h, A, nrhs, xcap_of(h), h->nb, st, [&](typename P::Args& X, int r0) {
-      X.r += (long long)r0 * h->nf;
-      X.z += (long long)r0 * h->nf;
-      X.t += (long long)r0 * tstride;
-    });
+    cudaError_t e = allow_dynamic_smem((const void*)kern, smem);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    const int grid = (int)std::min<long long>(h->nl, (long long)h->nsm * std::max(occ, 1));
+    for (int rhs = 0; rhs < nrhs && e == cudaSuccess; ++rhs) {
+      A.r = r + (long long)rhs * h->nf;
+      A.z = z + (long long)rhs * h->nf;
+      A.t = t + (long long)rhs * tstride;
+      kern<<<grid, kThreads, smem, st>>>(A);
+      ++h->prof.launches;
+      e = cudaGetLastError();
+    }
     h->prof.end(HPS_PHASE_PRECOND_B, ev, st);
     if (e != cudaSuccess) return e;
   }

@@ -195,7 +195,8 @@ struct Profiler {
 };
 
 // The paper's iterative path on the global system (Sec. 3-4): per distinct
-// (binned) homogenized constant S~^{-1} = (A~^{-1})_bb, row-major nb x nb, and
+// (binned) homogenized constant S~^{-1} = (A~^{-1})_bb, nb x nb stored transposed
+// (column-major), and
 // per axis the Algorithm 3 tables V (n1 x n1), V^{-1}, E (n1), row-major.
 struct FullSystem {
   bool built = false;

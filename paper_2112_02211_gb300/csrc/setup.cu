@@ -461,7 +461,9 @@ __global__ void lambda_kernel(const double2* c, int ni, double2* lam) {
   }
 }
 
-// B^leaf = R~^leaf[internal face rows][external face cols] for the leaves of a batch.
+// B^leaf = R~^leaf[internal face rows][external face cols] for the leaves of a batch,
+// stored transposed (column-major: column c holds the nint q^2 rows, ld rup4(nint q^2))
+// so that stage B reads it with one thread per row, coalesced.
 template <class T>
 __global__ void extract_b_kernel(const T* Rt, long long rstride, int ldr, const int* leaf_ids,
                                  int nbatch, int q, const uint8_t* int_mask, const long long* b_off,
@@ -478,7 +480,7 @@ __global__ void extract_b_kernel(const T* Rt, long long rstride, int ldr, const 
   for (int f = 0; f < 6; ++f) {
     if (mask & (1u << f)) ifaces[a++] = f; else efaces[e++] = f;
   }
-  const int ldb = (int)rup4(next * q2);
+  const int ldt = (int)rup4(nint * q2);
   const long long off = b_off[leaf];
   const long long total = (long long)nint * q2 * next * q2;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -486,7 +488,7 @@ __global__ void extract_b_kernel(const T* Rt, long long rstride, int ldr, const 
     const int r = (int)(t / (next * q2)), c = (int)(t % (next * q2));
     const int rf = ifaces[r / q2], cf = efaces[c / q2];
     const T v = Rt[(long long)b * rstride + (long long)(rf * q2 + r % q2) * ldr + cf * q2 + c % q2];
-    const long long o = off + (long long)r * ldb + c;
+    const long long o = off + (long long)c * ldt + r;  // stored transposed: column c, row r
     if (B64) B64[o] = cvt<double2>(v);
     if (B32) B32[o] = cvt<float2>(v);
   }
@@ -644,7 +646,8 @@ __global__ void quantize_kc_ws_kernel(const float2* W, long long wstride, int ld
                  kscale + (long long)s0 * q2 + r, lane);
 }
 
-// rows of every distinct B block; row index (block*6 + face)*q^2 + j for internal faces
+// rows of every distinct B block (stored transposed); row index (block*6 + face)*q^2 + j
+// for internal faces: divided by its largest |re|, |im| and rounded to FP16.
 __global__ void quantize_b_kernel(const float2* B32, __half2* B16, float* bscale, const int* bc_rep,
                                   const uint8_t* int_mask, const long long* b_off, int q2, long long nrows) {
   const int lane = threadIdx.x & 31;
@@ -655,10 +658,24 @@ __global__ void quantize_b_kernel(const float2* B32, __half2* B16, float* bscale
     const int j = (int)(gr % q2);
     const unsigned mask = int_mask[leaf];
     if (!(mask & (1u << face))) continue;
+    const int nint = __popc(mask);
     const int rb = __popc(mask & ((1u << face) - 1u));
-    const int ncols = (6 - __popc(mask)) * q2;
-    const long long off = b_off[leaf] + (long long)(rb * q2 + j) * rup4(ncols);
-    quantize_row(B32 + off, B16 + off, ncols, bscale + gr, lane);
+    const int ncols = (6 - nint) * q2, ldr = (int)rup4(nint * q2), row = rb * q2 + j;
+    const long long off = b_off[leaf] + row;
+    float m = 0.f;
+    for (int c = lane; c < ncols; c += 32) {
+      const float2 v = B32[off + (long long)c * ldr];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const float sc = (m > 0.f) ? m : 1.f;
+    const float inv = 1.f / sc;
+    for (int c = lane; c < ncols; c += 32) {
+      const float2 v = B32[off + (long long)c * ldr];
+      B16[off + (long long)c * ldr] = __floats2half2_rn(v.x * inv, v.y * inv);
+    }
+    if (lane == 0) bscale[gr] = sc;
   }
 }
 
@@ -971,7 +988,7 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
   for (int k = 0; k < ct.nbc; ++k) {
     const int ni_ = __builtin_popcount(ct.int_mask[ct.bc_rep[k]]);
     bc_off[k] = off;
-    off += (long long)ni_ * q2 * round_up((long long)(6 - ni_) * q2, 4);
+    off += (long long)(6 - ni_) * q2 * round_up((long long)ni_ * q2, 4);
   }
   ct.b_elems = off;
   ct.b_off.assign(h->nl, 0);
@@ -1326,8 +1343,9 @@ __global__ void extract_sinv_kernel(const double2* W, long long wstride, int ld,
        t += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(t / nb), c = (int)(t % nb);
     const double2 v = W[(long long)b * wstride + (long long)(ni + r) * ld + n + c];
-    if (S64) S64[off + t] = v;
-    if (S32) S32[off + t] = make_float2((float)v.x, (float)v.y);
+    const long long o = off + (long long)c * nb + r;  // stored transposed: column c holds the rows
+    if (S64) S64[o] = v;
+    if (S32) S32[o] = make_float2((float)v.x, (float)v.y);
   }
 }
 
