@@ -234,19 +234,24 @@ struct PrecKP {
     int nrhs;  // group width of the launch
     long long nitems;
   };
+  // item (k, s * kKRowSplit + part, first member, members): rows
+  // [part * hq, min(q^2, (part + 1) * hq)) of slot s, hq = ceil(q^2 / kKRowSplit)
   __device__ static bool decode(const Args& A, long long item, ItemInfo& it) {
     const int4 e = A.items[item];
-    const int k = e.x, s = e.y;
+    const int k = e.x, s = e.y / kKRowSplit, part = e.y % kKRowSplit;
+    const int hq = (A.q2 + kKRowSplit - 1) / kKRowSplit;
+    const int r0 = min(A.q2, part * hq);
     const int s0 = A.kc_slot_begin[k], ns = A.kc_slot_begin[k + 1] - s0;
     it.ncols = ns * A.q2;
     it.ld = (int)rup4(it.ncols);
-    it.mat = A.K + A.kc_off[k] + (long long)s * A.q2 * it.ld;
-    it.nrows = A.q2;
+    it.mat = A.K + A.kc_off[k] + ((long long)s * A.q2 + r0) * it.ld;
+    it.nrows = min(A.q2, r0 + hq) - r0;
     it.face = s;
+    it.nbr = r0;    // first row within the slot
     it.xoff = e.z;  // first member
     it.mask = e.w;  // members
-    it.aoff = (long long)(s0 + s) * A.q2;
-    return true;
+    it.aoff = (long long)(s0 + s) * A.q2 + r0;
+    return it.nrows > 0;
   }
   __device__ static Acc load_x(const Args& A, const ItemInfo& it, int rr, int c) {
     if (rr >= it.mask) return czero<Acc>();
@@ -254,12 +259,12 @@ struct PrecKP {
     return cvt<Acc>(A.t[A.cl_tpos[cl] + c]);
   }
   __device__ static void store(const Args& A, const ItemInfo& it, const Acc* outs, int, int tid) {
-    for (int idx = tid; idx < it.mask * A.q2; idx += kThreads) {
-      const int rr = idx / A.q2, j = idx % A.q2;
+    for (int idx = tid; idx < it.mask * it.nrows; idx += kThreads) {
+      const int rr = idx / it.nrows, jj = idx % it.nrows;
       const int cl = A.members[it.xoff + rr];
       const int lf = A.slot_lf[A.cl_slot_begin[cl] + it.face];
-      const long long o = (long long)(lf / 6) * A.nb + (long long)(lf % 6) * A.q2 + j;
-      A.z[o] = cvt<TOUT>(rscale(outs[idx], A.kscale, it.aoff + j));
+      const long long o = (long long)(lf / 6) * A.nb + (long long)(lf % 6) * A.q2 + it.nbr + jj;
+      A.z[o] = cvt<TOUT>(rscale(outs[idx], A.kscale, it.aoff + jj));
     }
   }
   __device__ static void copy(const Args&, const ItemInfo&, int, int) {}

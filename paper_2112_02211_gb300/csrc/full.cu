@@ -14,8 +14,7 @@
 //             y = A~_ii^{-1} r_i by Algorithm 3 (mode products with V^{-1},
 //             division by -(E_x + E_y + E_z) - lambda, mode products with V),
 //             z_b = S~^{-1} (r_b - F_bi y), z_i = A~_ii^{-1} (r_i - A_ib z_b);
-//             S~^{-1} = (A~^{-1})_bb per distinct (binned) lambda from setup,
-//             stored transposed for a thread-per-row product.
+//             S~^{-1} = (A~^{-1})_bb per distinct (binned) lambda from setup.
 //
 // One CTA per (right-hand side, leaf); the leaf's vector is staged in shared
 // memory; neighbour values needed by the coupling rows are read from global
@@ -257,6 +256,7 @@ __global__ void __launch_bounds__(kFT) full_precond_kernel(FullPrecArgs a) {
   const TIN* rin = reinterpret_cast<const TIN*>(a.r);
   TOUT* zo = reinterpret_cast<TOUT*>(a.z);
   const TS* S = reinterpret_cast<const TS*>(a.S);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long items = (long long)a.G.nl * a.nrhs;
   for (long long item = blockIdx.x; item < items; item += gridDim.x) {
     const int rhs = (int)(item / a.G.nl), leaf = (int)(item % a.G.nl);
@@ -282,14 +282,15 @@ __global__ void __launch_bounds__(kFT) full_precond_kernel(FullPrecArgs a) {
       wb[jb] = csub(rs[ni + jb], acc);
     }
     __syncthreads();
-    // z_b = S~^{-1} w_b: one thread per row, S~^{-1} stored transposed (column c holds the
-    // rows), so a warp reads 32 consecutive rows of one column
+    // z_b = S~^{-1} w_b (one warp per row, lanes over columns; a thread per row on a
+    // transposed S~^{-1} was measured slower: its 384-term dependent chain per thread)
     const TS* Sk = S + (long long)a.cls[leaf] * nb * nb;
-    for (int row = threadIdx.x; row < nb; row += kFT) {
+    for (int row = warp; row < nb; row += kFT / 32) {
       C acc = czero<C>();
-#pragma unroll 4
-      for (int c = 0; c < nb; ++c) cfma(acc, cvt<C>(Sk[(long long)c * nb + row]), wb[c]);
-      zb[row] = acc;
+      for (int c = lane; c < nb; c += 32) cfma(acc, cvt<C>(Sk[(long long)row * nb + c]), wb[c]);
+      acc.x = warp_sum(acc.x);
+      acc.y = warp_sum(acc.y);
+      if (lane == 0) zb[row] = acc;
     }
     __syncthreads();
     // t2 = r_i - A_ib z_b: A_ib holds -D2 at the line ends (face nodes)

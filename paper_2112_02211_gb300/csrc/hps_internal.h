@@ -86,10 +86,10 @@ struct ClusterTables {
   int nbc = 0;
   std::vector<int> leaf_bcls;        // [nleaves] B block of each leaf; FP16 scale row = (bcls*6 + face) q^2 + j
   std::vector<int> bc_rep;           // [nbc] first leaf using the block
-  // stage-K work items (block, block slot, first member, member count) for
-  // member groups of width 1, 2, 4 and 8, and the blocks whose members are
-  // many enough for the tensor-core path (tc_precond.cu), which then skip the
-  // items above
+  // stage-K work items (block, block slot * kKRowSplit + part of its rows,
+  // first member, member count) for member groups of width 1, 2, 4 and 8, and
+  // the blocks whose members are many enough for the tensor-core path
+  // (tc_precond.cu), which then skip the items above
   std::vector<int4> kitems[4];
   long long kitems_ntc[4] = {0, 0, 0, 0};
   std::vector<int> kc_tc;
@@ -195,8 +195,7 @@ struct Profiler {
 };
 
 // The paper's iterative path on the global system (Sec. 3-4): per distinct
-// (binned) homogenized constant S~^{-1} = (A~^{-1})_bb, nb x nb stored transposed
-// (column-major), and
+// (binned) homogenized constant S~^{-1} = (A~^{-1})_bb, row-major nb x nb, and
 // per axis the Algorithm 3 tables V (n1 x n1), V^{-1}, E (n1), row-major.
 struct FullSystem {
   bool built = false;
@@ -312,6 +311,9 @@ void build_cluster_tables(hps_handle* h, int width);
 void assign_blocks(hps_handle* h, const std::vector<double2>* lamq);
 // Shared K blocks with at least this many member clusters run on the tensor cores.
 constexpr int kTcMinMembers = 16;
+// Stage-K work items of the SIMT kernel cover 1/kKRowSplit of a slot's q^2 rows
+// (finer items balance the last wave of the launch).
+constexpr int kKRowSplit = 2;
 
 // ---- apply.cu ----
 // C128 complex double, C64 complex float, DF complex double-float (float4: re.h, im.h, re.l, im.l)

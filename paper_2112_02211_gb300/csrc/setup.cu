@@ -1120,7 +1120,9 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
         const int cnt = std::min(end - pos, wmax);
         int bucket = 0;
         while ((1 << bucket) < cnt) ++bucket;
-        for (int sl = 0; sl < ns; ++sl) ct.kitems[bucket].push_back(make_int4(k, sl, pos, cnt));
+        for (int sl = 0; sl < ns; ++sl)
+          for (int part = 0; part < kKRowSplit; ++part)
+            ct.kitems[bucket].push_back(make_int4(k, sl * kKRowSplit + part, pos, cnt));
         pos += cnt;
       }
     }
@@ -1343,9 +1345,8 @@ __global__ void extract_sinv_kernel(const double2* W, long long wstride, int ld,
        t += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(t / nb), c = (int)(t % nb);
     const double2 v = W[(long long)b * wstride + (long long)(ni + r) * ld + n + c];
-    const long long o = off + (long long)c * nb + r;  // stored transposed: column c holds the rows
-    if (S64) S64[o] = v;
-    if (S32) S32[o] = make_float2((float)v.x, (float)v.y);
+    if (S64) S64[off + t] = v;
+    if (S32) S32[off + t] = make_float2((float)v.x, (float)v.y);
   }
 }
 
