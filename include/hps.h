@@ -97,7 +97,9 @@ typedef struct {
                          blocks; see lambda_bin); default 1 */
   int lean;           /* memory-lean mixed form (forms must be HPS_FORM_MIXED): the exact leaf
                          maps R, H are eliminated in FP64 but kept only in FP32, the cluster
-                         inverses only in FP16, and the restart residual uses the FP32 maps with
+                         inverses only in FP16 (plus complex-FP32 copies of blocks shared by
+                         >= 16 clusters when they take <= 4 GiB, for the tensor-core path),
+                         and the restart residual uses the FP32 maps with
                          FP64 vectors (about 1e-7 relative per apply, for tolerances >= 1e-5).
                          HPS_C128 applies are then unavailable.  Default 0. */
   double lambda_bin;  /* shared preconditioner blocks (Sec. 4.1 remark: one local solver for

@@ -302,8 +302,11 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
         HPS_CUDA_TRY(cudaMemsetAsync(h->B64, 0, be * sizeof(double2), st));
       }
       const bool fp16 = want32 && (o.precond_fp16 || o.lean);
+      // lean mode keeps K_c only in FP16, except when the shared blocks are few enough that
+      // their complex-FP32 copies (needed by the tensor-core stage K) take at most 4 GiB
+      const bool kc32 = !o.lean || (!ct.kc_tc.empty() && ke * sizeof(float2) <= ((size_t)4 << 30));
       if (want32) {
-        if (!o.lean && (r = dalloc(h, (void**)&h->Kc32, ke * sizeof(float2)))) return r;
+        if (kc32 && (r = dalloc(h, (void**)&h->Kc32, ke * sizeof(float2)))) return r;
         if ((r = dalloc(h, (void**)&h->B32, be * sizeof(float2)))) return r;
         if (h->Kc32) HPS_CUDA_TRY(cudaMemsetAsync(h->Kc32, 0, ke * sizeof(float2), st));
         HPS_CUDA_TRY(cudaMemsetAsync(h->B32, 0, be * sizeof(float2), st));
@@ -371,6 +374,8 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
              (size_t)h.nl * 6 * sizeof(long long);  // stage-B offsets, t positions
     if (want64) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c16;
     if (want32) bytes += (size_t)((o.lean ? 0 : ct.kc_elems) + ct.b_elems) * c8;
+    if (want32 && o.lean)  // complex-FP32 copies of shared blocks (if any), capped
+      bytes += std::min<size_t>((size_t)ct.kc_elems * c8, (size_t)4 << 30);
     if (want32 && (o.precond_fp16 || o.lean))
       bytes += (size_t)(ct.kc_elems + ct.b_elems) * sizeof(__half2) + nslots * q2 * sizeof(float) +
                (size_t)h.nl * 6 * q2 * sizeof(float);

@@ -76,7 +76,8 @@ def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
 def large_solve(L=32, steps=3, warmup=1):
     """The large single solve: 32^3 leaves, p = 10, kappa = eta = 200, smooth random complex
     medium, Gaussian source of width 0.01 at the centre, tol 1e-5, lean mixed form (FP32 maps,
-    FP16 cluster inverses, double-float Krylov basis).  Returns setup time, memory and the
+    FP16 cluster inverses shared at lambda_bin 0.01, double-float Krylov basis).  Returns setup
+    time, memory and the
     per-solve time, iterations and throughput (face unknowns/s), inputs resident on the GPU."""
     import time
 
@@ -90,7 +91,7 @@ def large_solve(L=32, steps=3, warmup=1):
     b = w.sample_b(xi)
     s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
     t0 = time.time()
-    solver = Solver(L, L, L, w.p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",), lean=True)
+    solver = Solver(L, L, L, w.p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",), lean=True, lambda_bin=0.01)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     try:

@@ -164,3 +164,30 @@ def _masks(grid):
         for leaf in leaves:
             out.append(sum(1 << f for f in range(6) if grid.neighbor(leaf, f) in members))
     return out
+
+
+def test_lean_mode_keeps_shared_blocks_on_tensor_cores(tc_case):
+    """Lean mode keeps FP16 blocks for the SIMT stage and complex-FP32 copies of the widely
+    shared blocks for the tensor cores; both preconditioner forms and the lean solve meet
+    the bars of the non-lean handle."""
+    w, grid, M, b, t = tc_case
+    rng = np.random.default_rng(19)
+    r = (rng.standard_normal(grid.nf) + 1j * rng.standard_normal(grid.nf)).astype(np.complex64)
+    ref = M(r.astype(np.complex128))
+    solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",), lean=True)
+    try:
+        assert solver.precond_info() == (96, 2, len({(m,) for m in _masks(grid)}))
+        z = solver.precond(torch.from_numpy(r).cuda()).cpu().numpy()
+        assert rel(z, ref) < 5e-3
+        z16 = solver.precond(torch.from_numpy(r).cuda(), fp16_blocks=True).cpu().numpy()
+        assert rel(z16, ref) < 5e-3
+        f, info = solver.solve(t=torch.from_numpy(t.reshape(-1)).cuda(), tol=1e-7, form="mixed")
+        assert info["converged"], info
+        xi, xf = O.interior_nodes(grid), O.face_nodes(grid)
+        nrm = np.broadcast_to(O.face_normals()[None, :, None, :], xf.shape)
+        prob = O.build_problem(grid, w.kappa, w.eta, w.sample_b(xi))
+        rhs = O.rhs_face(grid, prob.H, None, w.sample_t(xf, nrm)[0])
+        f_ref, _, _ = O.gmres(lambda v: O.apply_face(grid, prob.R, v), rhs, tol=1e-12, restart=50)
+        assert rel(f.cpu().numpy(), f_ref) < 1e-5
+    finally:
+        solver.close()
