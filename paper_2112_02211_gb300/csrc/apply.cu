@@ -559,6 +559,10 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
 
 }  // namespace
 
+bool apply_tc_eligible(const hps_handle* h, int nrhs) {
+  return h->opt.tc_apply && h->tc_error && h->R32 && nrhs >= 64 && nrhs % 64 == 0;
+}
+
 cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const void* f, VType tout, void* y,
                          const double2* bvec, int nrhs, bool residual, cudaStream_t st) {
   if (!residual) bvec = nullptr;
@@ -569,7 +573,7 @@ cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const
   }
   // the residual form b - (I + Pi R) f only exists for complex-double vectors
   if (bvec && !(tin == VType::C128 && tout == VType::C128)) return cudaErrorInvalidValue;
-  const bool tc = h->opt.tc_apply && h->tc_error && nrhs >= 64 && nrhs % 64 == 0 && !bvec;
+  const bool tc = apply_tc_eligible(h, nrhs) && !bvec;
   if (tc && tin == VType::C64 && tout == VType::C64)
     return launch_apply_tc(h, (const float2*)f, y, false, nrhs, h->tc_error, st);
   if (tc && tin == VType::C64 && tout == VType::DF)

@@ -328,6 +328,8 @@ cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, con
                            VType tout, void* z, void* scratch, int nrhs, cudaStream_t st, bool fp16_blocks = false);
 // Tensor-core apply for 64-RHS groups (tc_apply.cu); f complex float, y complex
 // float or double-float; nrhs a multiple of 64.
+// whether launch_apply runs nrhs right-hand sides with complex-FP32 input on the tensor cores
+bool apply_tc_eligible(const hps_handle* h, int nrhs);
 cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool out_df, int nrhs, int* d_error,
                             cudaStream_t st);
 // Stage K of the preconditioner for the shared K blocks listed in ct.kc_tc, on
@@ -355,6 +357,9 @@ struct GmresOps {
   std::function<cudaError_t(VType, const void*, VType, void*, int, cudaStream_t)> apply;
   std::function<cudaError_t(VType, const void*, VType, void*, int, cudaStream_t)> precond;
   std::function<cudaError_t(const double2*, const double2*, double2*, int, cudaStream_t)> residual;
+  // mixed form without a preconditioner: the apply takes the basis vector rounded to complex
+  // FP32 (kept beside the double-float basis) instead of the double-float vector itself
+  bool c64_operand = false;
 };
 int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b, double2* x, int nrhs, double tol,
                hps_solve_info* info, cudaStream_t st);

@@ -349,23 +349,29 @@ __global__ void __launch_bounds__(kT) axpy_df_kernel(DfArgs a, int mode) {
   }
 }
 
-// w <- w * invn[rhs] in double-float
-__global__ void scale_df_kernel(float4* w, long long nf, const double* invn) {
+// w <- w * invn[rhs] in double-float; c32 (if given) receives the result rounded to complex FP32
+// (the normalized double-float's high part), the operand of the tensor-core apply
+__global__ void scale_df_kernel(float4* w, long long nf, const double* invn, float2* c32) {
   const int rhs = blockIdx.y;
   const dfr s = df_from_double(invn[rhs]);
   float4* p = w + rhs * nf;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
     const dfc v = dfc_load(p[i]);
-    p[i] = dfc_store(dfc{df_mul(v.re, s), df_mul(v.im, s)});
+    const dfc r = dfc{df_mul(v.re, s), df_mul(v.im, s)};
+    p[i] = dfc_store(r);
+    if (c32) c32[rhs * nf + i] = make_float2(r.re.h, r.im.h);
   }
 }
 
-// dst (double-float) = src (complex double) * invn[rhs]
-__global__ void scale_copy_df_kernel(const double2* src, float4* dst, long long nf, const double* invn) {
+// dst (double-float) = src (complex double) * invn[rhs]; c32 as in scale_df_kernel
+__global__ void scale_copy_df_kernel(const double2* src, float4* dst, long long nf, const double* invn, float2* c32) {
   const int rhs = blockIdx.y;
   const double s = invn[rhs];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x)
-    dst[rhs * nf + i] = dfc_store(dfc_from(cscale(src[rhs * nf + i], s)));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
+    const dfc r = dfc_from(cscale(src[rhs * nf + i], s));
+    dst[rhs * nf + i] = dfc_store(r);
+    if (c32) c32[rhs * nf + i] = make_float2(r.re.h, r.im.h);
+  }
 }
 
 // u (complex double) = sum_{j<kmax} y_j v_j, accumulated in double-float
@@ -716,8 +722,10 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
         HPS_CUDA_TRY(cudaMemcpyAsync(k.g + (long long)r * M1, &g0[r], sizeof(double2), cudaMemcpyHostToDevice, st));
       HPS_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    // unpreconditioned mixed form with a complex-FP32 operand: v_j is also kept rounded in z
+    float2* vc32 = (mixed && !pc && ops.c64_operand) ? (float2*)k.z : nullptr;
     if (mixed)
-      scale_copy_df_kernel<<<vgrid, 256, 0, st>>>(k.r, (float4*)k.V, nf, invn);
+      scale_copy_df_kernel<<<vgrid, 256, 0, st>>>(k.r, (float4*)k.V, nf, invn, vc32);
     else
       scale_copy_kernel<<<vgrid, 256, 0, st>>>(k.r, k.V, nf, invn);
     HPS_CUDA_TRY(cudaGetLastError());
@@ -731,6 +739,8 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
       if (pc) {
         HPS_CUDA_TRY(ops.precond(vt, vj, zt, k.z, nrhs, st));
         HPS_CUDA_TRY(ops.apply(zt, k.z, vt, w, nrhs, st));
+      } else if (vc32) {
+        HPS_CUDA_TRY(ops.apply(VType::C64, vc32, vt, w, nrhs, st));
       } else {
         HPS_CUDA_TRY(ops.apply(vt, vj, vt, w, nrhs, st));
       }
@@ -797,7 +807,7 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
       ga.any_active = any_active;
       givens_kernel<<<nrhs, 64, 0, st>>>(ga);
       HPS_CUDA_TRY(cudaGetLastError());
-      if (mixed) scale_df_kernel<<<vgrid, 256, 0, st>>>((float4*)w, nf, invn);
+      if (mixed) scale_df_kernel<<<vgrid, 256, 0, st>>>((float4*)w, nf, invn, vc32);
       else scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);
       HPS_CUDA_TRY(cudaGetLastError());
       h->prof.end(HPS_PHASE_ARNOLDI, ev_arn, st);
@@ -879,6 +889,7 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
   ops.residual = [h](const double2* xx, const double2* bb, double2* r, int nrhs, cudaStream_t s) {
     return timed_apply(h, HPS_PHASE_RESIDUAL, h->R64 == nullptr, VType::C128, xx, VType::C128, r, bb, nrhs, true, s);
   };
+  ops.c64_operand = mixed && apply_tc_eligible(h, nrhs);
   return gmres_core(h, ops, mixed, b, x, nrhs, tol, info, st);
 }
 

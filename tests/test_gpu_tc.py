@@ -54,7 +54,9 @@ def test_tc_apply_matches_oracle_and_simt(shape, p):
 
 
 def test_tc_multi_rhs_solve():
-    """64 right-hand sides through the mixed solve (tensor-core apply inside GMRES)."""
+    """64 right-hand sides through the unpreconditioned mixed solve: each basis vector is also kept
+    rounded to complex FP32, which the tensor-core apply takes as its operand.  The same solve with
+    the SIMT apply (double-float operand) reaches the same solution by different arithmetic."""
     w, oc, tc, simt, (s, t) = _case(2, 2, 2, 7, 9.0)
     try:
         rng = np.random.default_rng(5)
@@ -69,6 +71,11 @@ def test_tc_multi_rhs_solve():
         for r in (0, 17, 63):
             ref = np.linalg.solve(M, O.rhs_face(oc.grid, oc.prob.H, S[r], T[r]))
             assert rel(f[r], ref) < 1e-7, r
+        f2, info2 = simt.solve(s=torch.from_numpy(S.reshape(-1)).cuda(), t=torch.from_numpy(T.reshape(-1)).cuda(),
+                               tol=1e-9, form="mixed", nrhs=64)
+        assert info2["converged"], info2
+        f2 = f2.cpu().numpy().reshape(64, -1)
+        assert 0 < rel(f, f2) < 1e-7
     finally:
         tc.close()
         simt.close()
