@@ -76,9 +76,10 @@ def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
 def large_solve(L=32, steps=3, warmup=1):
     """The large single solve: 32^3 leaves, p = 10, kappa = eta = 200, smooth random complex
     medium, Gaussian source of width 0.01 at the centre, tol 1e-5, lean mixed form (FP32 maps,
-    FP16 cluster inverses shared at lambda_bin 0.01, double-float Krylov basis).  Returns setup
-    time, memory and the
-    per-solve time, iterations and throughput (face unknowns/s), inputs resident on the GPU."""
+    FP16 cluster inverses shared at lambda_bin 0.01 with complex-FP32 copies of the widely shared
+    ones for the tensor cores, double-float Krylov basis).  Returns setup time, memory, the
+    distinct blocks and the per-solve time, iterations and throughput (face unknowns/s), inputs
+    resident on the GPU."""
     import time
 
     import torch
@@ -109,10 +110,12 @@ def large_solve(L=32, steps=3, warmup=1):
         ms = e0.elapsed_time(e1) / steps
         prof = solver.profile(enable=False, reset=True)
         mem = solver.memory_bytes
+        blocks = solver.precond_info()
     finally:
         solver.close()
     return {"workload": f"large_{L}cubed", "leaves": L ** 3, "face_unknowns": solver.nf, "setup_s": setup_s,
-            "device_bytes": mem, "ms_per_solve": ms, "unknowns_per_s": solver.nf / (ms / 1e3),
+            "device_bytes": mem, "clusters_k_blocks_b_blocks": blocks, "ms_per_solve": ms,
+            "unknowns_per_s": solver.nf / (ms / 1e3),
             "iterations": info["iterations"], "rel_residual": info["rel_residual"],
             "phase_ms_per_solve": {k: v / steps for k, v in prof["ms"].items()}}
 
