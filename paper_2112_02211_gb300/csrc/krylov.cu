@@ -249,7 +249,41 @@ __device__ __forceinline__ void block_reduce_store_df(dfc (&part)[kG], int ng, d
   __syncthreads();
 }
 
+__device__ __forceinline__ dfc shfl_xor_dfc(dfc a, int o) {
+  dfc r;
+  r.re.h = __shfl_xor_sync(0xffffffffu, a.re.h, o);
+  r.re.l = __shfl_xor_sync(0xffffffffu, a.re.l, o);
+  r.im.h = __shfl_xor_sync(0xffffffffu, a.im.h, o);
+  r.im.l = __shfl_xor_sync(0xffffffffu, a.im.l, o);
+  return r;
+}
+
+// Warp sums of kG = 4 double-float complex partials per lane, in a fixed order and without
+// block barriers: a halving exchange (offset 16: lanes 0-15 keep groups 0, 1 and lanes 16-31
+// groups 2, 3; offset 8: one group per 8-lane segment) then three xor steps inside each segment.
+// Every lane l returns the warp's sum of group l >> 3.
+__device__ __forceinline__ dfc warp_reduce_groups(const dfc (&part)[kG]) {
+  static_assert(kG == 4, "halving exchange written for 4 groups");
+  const int lane = threadIdx.x & 31;
+  const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+  dfc k0 = hi16 ? part[2] : part[0], k1 = hi16 ? part[3] : part[1];
+  const dfc s0 = hi16 ? part[0] : part[2], s1 = hi16 ? part[1] : part[3];
+  k0 = dfc_add(k0, shfl_xor_dfc(s0, 16));
+  k1 = dfc_add(k1, shfl_xor_dfc(s1, 16));
+  dfc k = hi8 ? k1 : k0;
+  k = dfc_add(k, shfl_xor_dfc(hi8 ? k0 : k1, 8));
+  k = dfc_add(k, shfl_xor_dfc(k, 4));
+  k = dfc_add(k, shfl_xor_dfc(k, 2));
+  k = dfc_add(k, shfl_xor_dfc(k, 1));
+  return k;
+}
+
+// Partial dots V^H w of this block (one per basis vector, complex double): per group of kG
+// vectors each warp reduces its lanes' partials on its own; one barrier at the end sums the
+// warps in order.  nvec <= 64 (restart <= 60).
 __device__ __forceinline__ void df_dots(const DfArgs& a, int rhs, long long base, const dfc (&wv)[kE], double2* out) {
+  __shared__ dfc wred[kT / 32][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int g0 = 0; g0 < a.nvec; g0 += kG) {
     const int ng = min(kG, a.nvec - g0);
     dfc part[kG];
@@ -269,11 +303,19 @@ __device__ __forceinline__ void df_dots(const DfArgs& a, int rhs, long long base
       }
       part[g] = {acc2_value(re), acc2_value(im)};
     }
-    block_reduce_store_df(part, ng, out + g0);
+    const dfc sum = warp_reduce_groups(part);
+    if ((lane & 7) == 0 && (lane >> 3) < ng) wred[warp][g0 + (lane >> 3)] = sum;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < a.nvec; j += kT) {
+    dfc t = wred[0][j];
+#pragma unroll
+    for (int w = 1; w < kT / 32; ++w) t = dfc_add(t, wred[w][j]);
+    out[j] = dfc_to_double2(t);
   }
 }
 
-__global__ void __launch_bounds__(kT) mdot_df_kernel(DfArgs a) {
+__global__ void __launch_bounds__(kT, 4) mdot_df_kernel(DfArgs a) {
   const int rhs = blockIdx.y, blk = blockIdx.x;
   if (a.active && !a.active[rhs]) return;
   const long long base = (long long)blk * kChunk + threadIdx.x;
@@ -288,7 +330,7 @@ __global__ void __launch_bounds__(kT) mdot_df_kernel(DfArgs a) {
 }
 
 // w -= V coef; then (mode 1) partial dots V^H w, or (mode 2) partial ||w||^2.
-__global__ void __launch_bounds__(kT) axpy_df_kernel(DfArgs a, int mode) {
+__global__ void __launch_bounds__(kT, 4) axpy_df_kernel(DfArgs a, int mode) {
   const int rhs = blockIdx.y, blk = blockIdx.x;
   if (a.active && !a.active[rhs]) return;
   __shared__ dfc cf[64];
