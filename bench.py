@@ -159,7 +159,8 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------------------------
-# algorithmic bytes per launch ("Roofline")
+# algorithmic bytes per launch: the bytes each kernel must move at least (matrix entries read
+# once, vectors read and written once), the numerator of the roofline fraction
 # --------------------------------------------------------------------------------------------
 def interior_face_pairs(L):
     return 6 * L ** 3 - 6 * L * L
