@@ -6,7 +6,7 @@
 //  * apply    y = A u, A of eq. (2x2): per leaf the interior rows
 //             -(D_x^2 + D_y^2 + D_z^2) u - C u along the three lines through
 //             each interior node (eq. (leafmat), the mode products of
-//             Algorithm 1, line ends on the face nodes), the face rows
+//             Algorithm 1; each grid line ends on two face nodes), the face rows
 //             F u = N u + i eta u, and on a face shared with beta the
 //             neighbour's outgoing data G^beta u^beta = N^beta u^beta - i eta u^beta
 //             at the same points (Algorithm 2, eq. (inter)).
