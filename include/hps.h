@@ -92,7 +92,9 @@ typedef struct {
   int precond_fp16;   /* mixed form: also keep the preconditioner blocks in FP16 with one FP32
                          scale per row and use them in hps_gmres_solve (default 1) */
   int tc_apply;       /* tensor cores (three TF32 products, FP32 accumulation) for the
-                         complex-FP32 apply of 64, 128, ... right-hand sides and for
+                         complex-FP32 apply of 64, 128, ... right-hand sides (inside an
+                         unpreconditioned mixed solve the Krylov vectors are also kept rounded
+                         to complex FP32 for it) and, with one TF32 product, for
                          preconditioner blocks shared by >= 16 clusters (complex-FP32
                          blocks; see lambda_bin); default 1 */
   int lean;           /* memory-lean mixed form (forms must be HPS_FORM_MIXED): the exact leaf
