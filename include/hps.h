@@ -286,6 +286,22 @@ int hps_full_solve(hps_handle* h, int form, const double* s, const double* t, in
  */
 int hps_precond_info(const hps_handle* h, int* clusters, int* k_blocks, int* b_blocks);
 
+/*
+ * Host-only planning of the shared preconditioner blocks that hps_setup does
+ * after binning (Sec. 4.1 remark; no device work, no GPU needed).  lambda_q:
+ * the binned constants of every leaf, nx*ny*nz complex doubles (interleaved,
+ * leaf order ix + nx*(iy + ny*iz)).  Clusters are the 2x2x2 blocks of leaves
+ * (1-wide at the end of an odd axis), numbered x fastest.  A leaf's B block is
+ * keyed by (lambda_q, internal-face mask); a cluster's K_c block by the
+ * sequence of its leaves' keys; -0 and +0 are one key.  Blocks are numbered in
+ * order of first appearance.  Writes leaf_b_block[nx*ny*nz] and
+ * cluster_k_block[*clusters] (either may be NULL; the cluster count is
+ * ceil(nx/2)*ceil(ny/2)*ceil(nz/2)) and the counts (any may be NULL).
+ * HPS_EINVAL for an invalid grid, a NULL lambda_q or a non-finite constant.
+ */
+int hps_plan_blocks(const hps_grid* grid, const double* lambda_q, int* leaf_b_block, int* cluster_k_block,
+                    int* clusters, int* k_blocks, int* b_blocks);
+
 /* What hps_export copies out (host doubles, interleaved complex). */
 #define HPS_EXPORT_R 0      /* R^index, 6q^2 x 6q^2 row-major, FP64 */
 #define HPS_EXPORT_H 1      /* H^index, 6q^2 x n1^3 row-major */

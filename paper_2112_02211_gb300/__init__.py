@@ -19,7 +19,7 @@ import numpy as np
 from . import _native as N
 from ._native import HPSError
 
-__all__ = ["Solver", "nodes", "face_normals", "HPSError", "load"]
+__all__ = ["Solver", "nodes", "face_normals", "plan_blocks", "HPSError", "load"]
 
 load = N.load
 
@@ -52,6 +52,27 @@ def nodes(nx, ny, nz, p, cheb_faces=False):
     N.check(lib.hps_nodes(ctypes.byref(g), xi.ctypes.data_as(ctypes.c_void_p), xf.ctypes.data_as(ctypes.c_void_p),
                           None if xc is None else xc.ctypes.data_as(ctypes.c_void_p)))
     return (xi, xf, xc) if cheb_faces else (xi, xf)
+
+
+def plan_blocks(nx, ny, nz, p, lambda_q):
+    """Shared preconditioner blocks for the binned constants `lambda_q` (complex, one per leaf),
+    planned on the host as hps_setup does (no GPU): returns (B block of every leaf, K_c block of
+    every 2x2x2 cluster), both numbered in order of first appearance."""
+    lib = N.load()
+    lam = np.ascontiguousarray(np.asarray(lambda_q, dtype=np.complex128).reshape(-1))
+    nl = nx * ny * nz
+    if lam.size != nl:
+        raise ValueError(f"lambda_q has {lam.size} entries, expected {nl}")
+    ncl = -(-nx // 2) * -(-ny // 2) * -(-nz // 2)
+    leaf_b = np.zeros(nl, dtype=np.int32)
+    cl_k = np.zeros(ncl, dtype=np.int32)
+    g = N.Grid(nx, ny, nz, p, p - 2)
+    c = ctypes.c_int()
+    N.check(lib.hps_plan_blocks(ctypes.byref(g), lam.ctypes.data_as(ctypes.c_void_p),
+                                leaf_b.ctypes.data_as(ctypes.c_void_p), cl_k.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.byref(c), None, None))
+    assert c.value == ncl
+    return leaf_b, cl_k
 
 
 def face_normals():

@@ -658,6 +658,39 @@ int hps_precond_info(const hps_handle* h, int* clusters, int* k_blocks, int* b_b
   return HPS_OK;
 }
 
+int hps_plan_blocks(const hps_grid* g, const double* lambda_q, int* leaf_b_block, int* cluster_k_block,
+                    int* clusters, int* k_blocks, int* b_blocks) {
+  if (validate_grid(g)) return HPS_EINVAL;
+  if (!lambda_q) {
+    set_error("hps_plan_blocks: lambda_q is NULL");
+    return HPS_EINVAL;
+  }
+  hps_options o;
+  hps_default_options(&o);
+  hps_handle h;
+  init_fields(&h, g, 1.0, 1.0, o);
+  std::vector<double2> lamq(h.nl);
+  for (int i = 0; i < h.nl; ++i) {
+    const double re = lambda_q[2 * (size_t)i], im = lambda_q[2 * (size_t)i + 1];
+    if (!std::isfinite(re) || !std::isfinite(im)) {
+      set_error("hps_plan_blocks: non-finite constant");
+      return HPS_EINVAL;
+    }
+    lamq[i] = make_double2(re, im);
+  }
+  build_cluster_tables(&h, 2);
+  assign_blocks(&h, &lamq);
+  const ClusterTables& ct = h.ct;
+  if (leaf_b_block)
+    for (int i = 0; i < h.nl; ++i) leaf_b_block[i] = ct.leaf_bcls[i];
+  if (cluster_k_block)
+    for (int c = 0; c < ct.ncl; ++c) cluster_k_block[c] = ct.cl_class[c];
+  if (clusters) *clusters = ct.ncl;
+  if (k_blocks) *k_blocks = ct.nkc;
+  if (b_blocks) *b_blocks = ct.nbc;
+  return HPS_OK;
+}
+
 long long hps_export(hps_handle* h, int what, int index, double* host_out) {
   if (!h) {
     set_error("hps_export: NULL handle");
