@@ -302,6 +302,19 @@ int hps_precond_info(const hps_handle* h, int* clusters, int* k_blocks, int* b_b
 int hps_plan_blocks(const hps_grid* grid, const double* lambda_q, int* leaf_b_block, int* cluster_k_block,
                     int* clusters, int* k_blocks, int* b_blocks);
 
+/*
+ * Host-only: M = V diag(E) V^{-1} for a small real n x n matrix M with real,
+ * distinct eigenvalues -- the per-axis factorization L1 = V E V^{-1} that
+ * Algorithm 3 (Sec. 4.1) needs and hps_setup computes when full_system is set
+ * (no device work).  Shifted QR iteration with deflation for E, inverse
+ * iteration for the columns of V, Gauss-Jordan with partial pivoting for
+ * V^{-1}.  M, V, Vinv: host row-major n x n; E: host n; 1 <= n <= 64.
+ * HPS_EBREAKDOWN when the iteration does not converge (e.g. a complex pair)
+ * or when max|M V - V E| > 1e-9 max|M| or max|V V^{-1} - I| > 1e-9;
+ * HPS_EINVAL for bad arguments or a non-finite entry.
+ */
+int hps_axis_eig(int n, const double* M, double* V, double* Vinv, double* E);
+
 /* What hps_export copies out (host doubles, interleaved complex). */
 #define HPS_EXPORT_R 0      /* R^index, 6q^2 x 6q^2 row-major, FP64 */
 #define HPS_EXPORT_H 1      /* H^index, 6q^2 x n1^3 row-major */

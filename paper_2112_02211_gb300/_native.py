@@ -77,6 +77,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int)]),
     "hps_memory_bytes": (ctypes.c_size_t, [_P]),
     "hps_setup_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid), ctypes.POINTER(Options), ctypes.c_int]),
+    "hps_axis_eig": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P]),
     "hps_plan_blocks": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "hps_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),

@@ -691,6 +691,23 @@ int hps_plan_blocks(const hps_grid* g, const double* lambda_q, int* leaf_b_block
   return HPS_OK;
 }
 
+int hps_axis_eig(int n, const double* M, double* V, double* Vinv, double* E) {
+  if (n < 1 || n > 64 || !M || !V || !Vinv || !E) {
+    set_error("hps_axis_eig: n must be in 1..64 and no pointer NULL");
+    return HPS_EINVAL;
+  }
+  for (long long i = 0; i < (long long)n * n; ++i)
+    if (!std::isfinite(M[i])) {
+      set_error("hps_axis_eig: non-finite entry");
+      return HPS_EINVAL;
+    }
+  if (!axis_eig(n, M, V, Vinv, E)) {
+    set_error("hps_axis_eig: no real eigen-decomposition within its checks");
+    return HPS_EBREAKDOWN;
+  }
+  return HPS_OK;
+}
+
 long long hps_export(hps_handle* h, int what, int index, double* host_out) {
   if (!h) {
     set_error("hps_export: NULL handle");

@@ -298,6 +298,9 @@ int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st
 int compute_lambdas(hps_handle* h, const double2* cdiag, cudaStream_t st, std::vector<double2>& lamq);
 // S~^{-1} per distinct homogenized constant and the Algorithm 3 tables (full.cu uses them).
 int build_full_system(hps_handle* h, const double2* cdiag, cudaStream_t st);
+// M = V diag(E) V^{-1} for a small real matrix with real distinct eigenvalues (host; the
+// per-axis tables of Algorithm 3); false when it does not converge or fails its checks
+bool axis_eig(int n, const double* M, double* V, double* Vinv, double* E);
 int build_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st);
 int build_precond_fp16(hps_handle* h, cudaStream_t st);
 int recover_interior(hps_handle* h, const double2* s, const double2* f, int nrhs, double2* u, double2* uf,

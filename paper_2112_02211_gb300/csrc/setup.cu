@@ -1492,6 +1492,15 @@ bool small_eig(int n, const std::vector<double>& M, std::vector<double>& V, std:
 
 }  // namespace
 
+bool axis_eig(int n, const double* M, double* V, double* Vinv, double* E) {
+  std::vector<double> m(M, M + (size_t)n * n), v, vi, e;
+  if (!small_eig(n, m, v, vi, e)) return false;
+  std::copy(v.begin(), v.end(), V);
+  std::copy(vi.begin(), vi.end(), Vinv);
+  std::copy(e.begin(), e.end(), E);
+  return true;
+}
+
 int build_full_system(hps_handle* h, const double2* cdiag, cudaStream_t st) {
   FullSystem& fs = h->fs;
   const int n = h->n, ni = h->ni, nb = h->nb, n1 = h->n1, p = h->p;
