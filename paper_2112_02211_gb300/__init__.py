@@ -71,7 +71,8 @@ def plan_blocks(nx, ny, nz, p, lambda_q):
     N.check(lib.hps_plan_blocks(ctypes.byref(g), lam.ctypes.data_as(ctypes.c_void_p),
                                 leaf_b.ctypes.data_as(ctypes.c_void_p), cl_k.ctypes.data_as(ctypes.c_void_p),
                                 ctypes.byref(c), None, None))
-    assert c.value == ncl
+    if c.value != ncl:
+        raise HPSError(f"hps_plan_blocks returned {c.value} clusters, expected {ncl}")
     return leaf_b, cl_k
 
 
