@@ -72,7 +72,7 @@ def plan_blocks(nx, ny, nz, p, lambda_q):
                                 leaf_b.ctypes.data_as(ctypes.c_void_p), cl_k.ctypes.data_as(ctypes.c_void_p),
                                 ctypes.byref(c), None, None))
     if c.value != ncl:
-        raise HPSError(f"hps_plan_blocks returned {c.value} clusters, expected {ncl}")
+        raise HPSError(N.HPS_EINVAL, f"hps_plan_blocks returned {c.value} clusters, expected {ncl}")
     return leaf_b, cl_k
 
 
