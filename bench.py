@@ -66,12 +66,14 @@ def parse():
 # distributed plumbing (replicas only)
 # --------------------------------------------------------------------------------------------
 class Dist:
-    def __init__(self, backend=None):
+    def __init__(self, backend=None, group=True):
+        """Rank and world from the torchrun environment; a process group only when `group` (the
+        reference arm runs on rank 0 alone and needs none)."""
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
-        if self.world > 1:
+        if self.world > 1 and group:
             import torch.distributed as dist
             dist.init_process_group(backend=backend or "nccl")
             self.pg = dist
@@ -503,7 +505,7 @@ def run_reference(args, dist):
 
 def main():
     args = parse()
-    dist = Dist()
+    dist = Dist(group=args.impl != "reference")
     try:
         if args.impl == "reference":
             rec = run_reference(args, dist)

@@ -1,8 +1,11 @@
 """Host logic of bench.py's multi-rank path (replicas: barrier + max/sum of
-scalars, whole-job throughput), run as two gloo ranks on the CPU."""
+scalars, whole-job throughput), run as two gloo ranks on the CPU, and the
+reference arm's JSON line (the oracle on host cores), alone and under torchrun."""
 
+import json
 import os
 import socket
+import subprocess
 import sys
 
 import pytest
@@ -63,3 +66,38 @@ def test_algorithmic_bytes_formulas():
     assert kb == 512 * 1536 * 1536 * 8 + 512 * 1536 * 16
     kb16, _ = bench.precond_bytes(16, 8, 4, 8, in_bytes=16, scale_bytes=4)
     assert kb16 == 512 * 1536 * (1536 * 4 + 4) + 512 * 1536 * 16
+
+
+def _json_lines(out):
+    return [json.loads(line) for line in out.splitlines() if line.startswith("{")]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference`: the oracle on host cores, one JSON line with the contract's
+    keys; its cpu_baseline and e2e repeat the line's own value."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--cpu-sample-L", "2"], capture_output=True, text=True, timeout=600,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    (rec,) = _json_lines(r.stdout)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in rec, k
+    assert rec["impl"] == "reference" and rec["value"] > 0 and rec["steps"] == 1 and rec["n_gpus"] == 1
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["value"] == rec["value"]
+    assert rec["cpu_baseline"]["cores"] >= 1 and rec["cpu_baseline"]["sample"]
+    assert rec["e2e"] == {"value": rec["value"], "unit": rec["unit"], "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
+    assert rec["config"]["workload"].startswith("bump_16cubed")
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Two ranks: rank 0 alone runs the oracle and prints; the other exits 0 without work."""
+    port = _free_port()
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
+                        "--cpu-sample-L", "2"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    recs = _json_lines(r.stdout)
+    assert len(recs) == 1 and recs[0]["impl"] == "reference" and recs[0]["n_gpus"] == 2
