@@ -198,14 +198,18 @@ int hps_precond(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void
  * every device that loads it until the process exits.  A call needs
  * (internal face slots) * q^2 * nrhs * sizeof(element) bytes of it (for the
  * 16^3-leaf, p = 10 grid: 12.6 MB per complex-double right-hand side) and
- * returns HPS_EINVAL with a message when that exceeds the array.  The first
- * call on each device also looks up the array's device address (once per
- * device); make that first call before any stream capture begins.  The array
- * keeps whatever the last call left in it; nothing in it needs to start at
- * zero, because every call overwrites the part it reads.  All calls share the one
- * array: calls that may overlap on the GPU (other streams, other handles,
- * other host threads) race on it and must be serialized by the caller.
- * Arguments as in hps_precond.  Allocates no device memory.
+ * returns HPS_EINVAL with a message when that exceeds the array.  nrhs is not
+ * limited by options.max_rhs (the handle's scratch is not used), only by the
+ * array.  Every call looks up the array's device address on the current device
+ * (a host-side symbol lookup that allocates nothing); the first call on a
+ * device may load the library's device code, so make it before any stream
+ * capture begins.  The array keeps whatever the last call left in it; nothing
+ * in it needs to start at zero, because every call overwrites the part it
+ * reads.  All calls share the one array: calls that may overlap on the GPU
+ * (other streams, other handles, other host threads) race on it and must be
+ * serialized by the caller.  dtype: HPS_C128, HPS_C64 or HPS_C64_H16 with the
+ * same operator choices as hps_precond (HPS_C64 reads the FP16 copies when the
+ * handle keeps the cluster inverses in FP16 only).  Allocates no device memory.
  */
 #define HPS_PRECOND_NOALLOC_MAX_BYTES ((size_t)16 << 20)
 int hps_precond_noalloc(hps_handle* h, int dtype, const void* r, void* z, int nrhs, void* stream);
@@ -325,6 +329,18 @@ int hps_axis_eig(int n, const double* M, double* V, double* Vinv, double* E);
  * Returns the number of doubles written (>0) or a negative error code;
  * with host_out == NULL only the size is returned. */
 long long hps_export(hps_handle* h, int what, int index, double* host_out);
+
+/* Replaces the stored ItI map R^index of one leaf (Definition in Sec. 2.2: the
+ * map from incoming to outgoing impedance data on the leaf's six faces, Gauss
+ * basis) with a map supplied by the caller: host_in holds 6q^2 x 6q^2 complex
+ * doubles, row-major, interleaved, the layout hps_export writes.  The FP64
+ * copy is overwritten as given and the complex-FP32 copy with the values
+ * rounded to nearest.  Only what = HPS_EXPORT_R is accepted.  Use: checking
+ * the apply kernels against an independent operator, or a leaf map computed
+ * by another discretization of the same leaf.  The preconditioner and H are
+ * not changed.  Synchronous; HPS_EINVAL for a bad index, what or a
+ * non-finite entry. */
+int hps_import_map(hps_handle* h, int what, int index, const double* host_in);
 
 /* Phases timed by the profiler (indices into hps_profile.ms / count). */
 #define HPS_PHASE_APPLY 0     /* w = A z inside the Arnoldi loop (working precision) */

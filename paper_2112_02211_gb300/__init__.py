@@ -253,6 +253,13 @@ class Solver:
         N.check(self.lib.hps_export(self.handle, codes[what], index, buf.ctypes.data_as(ctypes.c_void_p)))
         return buf
 
+    def import_map(self, index, R):
+        """Replace leaf `index`'s stored ItI map with R (6q^2 x 6q^2 complex, host)."""
+        a = np.ascontiguousarray(np.asarray(R, dtype=np.complex128))
+        if a.shape != (self.nb, self.nb):
+            raise ValueError(f"R must be {self.nb} x {self.nb}")
+        N.check(self.lib.hps_import_map(self.handle, N.HPS_EXPORT_R, index, a.ctypes.data_as(ctypes.c_void_p)))
+
     def profile(self, enable=None, reset=False):
         """Per-phase device times (ms) and kernel launch count since the last reset."""
         if enable is not None:

@@ -69,6 +69,7 @@ SIGNATURES = {
                                        ctypes.POINTER(SolveInfo), _P]),
     "hps_recover": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "hps_export": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "hps_import_map": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "hps_full_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_full_precond": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_full_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P,

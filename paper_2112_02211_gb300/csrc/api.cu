@@ -790,6 +790,32 @@ long long hps_export(hps_handle* h, int what, int index, double* host_out) {
   return HPS_EINVAL;
 }
 
+int hps_import_map(hps_handle* h, int what, int index, const double* host_in) {
+  if (!h || !host_in) {
+    set_error("hps_import_map: NULL handle or input");
+    return HPS_EINVAL;
+  }
+  if (what != HPS_EXPORT_R || index < 0 || index >= h->nl) {
+    set_error("hps_import_map: only HPS_EXPORT_R with a leaf index in range is accepted");
+    return HPS_EINVAL;
+  }
+  if (int rc = check_finite(host_in, 2LL * h->nb * h->nb, "R")) return rc;
+  HPS_CUDA_TRY(cudaSetDevice(h->dev));
+  HPS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const size_t rows = h->nb, cols = h->nb;
+  if (h->R64) {
+    HPS_CUDA_TRY(cudaMemcpy2D(h->R64 + (size_t)index * h->nb * h->ldR, (size_t)h->ldR * sizeof(double2), host_in,
+                              cols * sizeof(double2), cols * sizeof(double2), rows, cudaMemcpyHostToDevice));
+  }
+  if (h->R32) {
+    std::vector<float2> tmp(rows * cols);
+    for (size_t i = 0; i < tmp.size(); ++i) tmp[i] = make_float2((float)host_in[2 * i], (float)host_in[2 * i + 1]);
+    HPS_CUDA_TRY(cudaMemcpy2D(h->R32 + (size_t)index * h->nb * h->ldR, (size_t)h->ldR * sizeof(float2), tmp.data(),
+                              cols * sizeof(float2), cols * sizeof(float2), rows, cudaMemcpyHostToDevice));
+  }
+  return HPS_OK;
+}
+
 int hps_profile_enable(hps_handle* h, int on) {
   if (!h) {
     set_error("hps_profile_enable: NULL handle");

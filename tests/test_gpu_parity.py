@@ -4,6 +4,7 @@ Tolerances (relative l2 unless stated):
 * leaf maps R, H (FP64 elimination on both sides, different pivot/rounding
   order): 1e-11;
 * hps_apply / hps_rhs in FP64: 1e-11 (dominated by the R difference above);
+  the apply alone on the oracle's own maps (hps_import_map): 1e-13;
   complex FP32 apply: 2e-6 (FP32 storage of R, ~6e-8 per entry, summed over
   6 q^2 terms with FP32 accumulation);
 * hps_precond: FP64 1e-9 (the cluster inverse amplifies the map difference by
@@ -81,6 +82,31 @@ def test_apply_matches_oracle(ragged, nrhs):
     y32 = solver.apply(f32).cpu().numpy().reshape(nrhs, -1)
     ref32 = np.stack([oc.apply(f[r].astype(np.complex64).astype(np.complex128)) for r in range(nrhs)])
     assert rel(y32, ref32) < 2e-6
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_apply_on_the_oracles_maps_fp64(nrhs):
+    """The apply kernel alone: the oracle's own leaf maps are loaded into a handle
+    (hps_import_map), so both sides apply the same R and only the summation order
+    differs.  Bar 1e-13 (6q^2 = 150 FP64 terms per row, ~1e-16 each)."""
+    w = _ragged_workload()
+    oc = OracleCase(w, with_precond=False)
+    xi, xf, b, s, t = gpu_inputs(w, hps)
+    solver = hps.Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=b, max_rhs=4, cluster=0)
+    try:
+        for leaf in range(oc.grid.nleaves):
+            solver.import_map(leaf, oc.prob.R[leaf])
+        for leaf in (0, oc.grid.nleaves - 1):
+            back = solver.export("R", leaf).reshape(oc.grid.nb, oc.grid.nb)
+            assert np.array_equal(back, oc.prob.R[leaf])
+        f = _rand(oc.grid.nf, 30 + nrhs, nrhs)
+        ref = np.stack([oc.apply(f[r]) for r in range(nrhs)])
+        y64 = solver.apply(torch.from_numpy(f.reshape(-1)).cuda()).cpu().numpy().reshape(nrhs, -1)
+        assert rel(y64, ref) < 1e-13
+        for r in range(nrhs):
+            assert rel(y64[r], ref[r]) < 1e-13, r
+    finally:
+        solver.close()
 
 
 @pytest.mark.parametrize("nrhs", [1, 2])
