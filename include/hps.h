@@ -68,9 +68,18 @@ extern "C" {
 /* Solve forms (bit flags for hps_options.forms). */
 #define HPS_FORM_FP64 1  /* everything in complex FP64 */
 #define HPS_FORM_MIXED 2 /* complex-FP32 apply/preconditioner inside FP64 Krylov + FP64 outer residual */
-/* OR'd into the form argument of hps_gmres_solve: run GMRES without the
- * preconditioner even when it was built (the solution is the same). */
+/* Flags OR'd into the form argument of hps_gmres_solve and hps_full_solve: */
+/* run GMRES without the preconditioner even when it was built (the solution is the same) */
 #define HPS_SOLVE_NO_PRECOND 16
+/* the output buffer holds an initial guess on entry (resume from a stored iterate): the
+ * first residual is b - A x0 instead of b */
+#define HPS_SOLVE_X0 32
+/* launch each Arnoldi step's kernels from the host, with one synchronization per step,
+ * instead of replaying the captured restart cycle (same arithmetic, same result bit for bit) */
+#define HPS_SOLVE_NO_GRAPH 64
+/* classical Gram-Schmidt twice at every step, instead of the second pass only where the
+ * DGKS test asks for it */
+#define HPS_SOLVE_CGS2 128
 
 typedef struct hps_handle hps_handle;
 
@@ -124,6 +133,8 @@ typedef struct {
   int converged;       /* 1 when every right-hand side met the tolerance */
   double rel_residual; /* max over RHS of ||b - A f||_2 / ||b||_2, FP64 operator */
   double seconds;      /* wall time of the solve (RHS build + GMRES), host clock */
+  int reorth_steps;    /* Arnoldi steps (summed over right-hand sides) that took the second
+                          Gram-Schmidt pass */
 } hps_solve_info;
 
 /* Fills *opt with the defaults listed above (forms = HPS_FORM_FP64|HPS_FORM_MIXED). */
@@ -228,11 +239,22 @@ int hps_rhs(hps_handle* h, const double* s, const double* t, int nrhs, double* b
  * right-hand side, with the FP64 operator.  form: HPS_FORM_FP64 (restarted
  * GMRES in FP64) or HPS_FORM_MIXED (complex-FP32 apply and preconditioner
  * inside an FP64 Krylov basis, with the true residual recomputed in FP64 at
- * every restart, which restores FP64 accuracy), optionally OR'd with
- * HPS_SOLVE_NO_PRECOND.  s, t as in hps_rhs; f_out:
- * nrhs*N_f complex doubles.  Pointers may be host or device memory (detected
- * per pointer; host buffers are copied inside the call).  info may be NULL.
- * The call returns after the result is in f_out.
+ * every restart, which restores FP64 accuracy), optionally OR'd with the
+ * HPS_SOLVE_* flags.  s, t as in hps_rhs; f_out: nrhs*N_f complex doubles
+ * (with HPS_SOLVE_X0 it holds the initial guess on entry).  Pointers may be
+ * host or device memory (detected per pointer; host buffers are copied inside
+ * the call).  info may be NULL.  The call returns after the result is in f_out.
+ *
+ * Each restart cycle (the first basis vector and `restart` Arnoldi steps:
+ * preconditioner, apply, Gram-Schmidt, Givens rotation, normalization) runs
+ * on the device without host synchronization: it is captured once per
+ * configuration as a CUDA graph (on the handle's own stream) and replayed on
+ * `stream`; a device flag written by each step's Givens kernel makes the
+ * kernels of the following steps return at once after convergence.  The host
+ * reads back once per cycle (residual norms and step counts).  Orthogonalization:
+ * one classical Gram-Schmidt pass, and a second one at the steps where the
+ * pass removed more than half of the vector's energy (DGKS criterion,
+ * ||w'|| < ||w||/sqrt(2)); HPS_SOLVE_CGS2 forces the second pass everywhere.
  */
 int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs,
                     double tol, double* f_out, hps_solve_info* info, void* stream);

@@ -160,9 +160,11 @@ class Solver:
         N.check(self.lib.hps_rhs(self.handle, _ptr(s), _ptr(t), nrhs, _ptr(out), _stream(stream)))
         return out
 
-    def solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=None, out=None, stream=None, precond=True):
+    def solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=None, out=None, stream=None, precond=True,
+              x0=None, graph=True, cgs2=False):
         """Solve (I + Pi R) f = tbar - Pi H s.  s, t, out: torch tensors (device or host) or numpy
-        arrays (host).  Returns (f, info dict)."""
+        arrays (host).  x0: initial guess (copied into out first).  graph=False launches every
+        Arnoldi step from the host; cgs2=True always orthogonalizes twice.  Returns (f, info dict)."""
         torch = _torch()
 
         def as_arg(a):
@@ -182,17 +184,26 @@ class Solver:
                 nrhs = 1
         if out is None:
             out = torch.empty(nrhs * self.nf, dtype=torch.complex128, device="cuda")
+        if x0 is not None:
+            if isinstance(out, np.ndarray):
+                out[...] = np.asarray(x0).reshape(out.shape)
+            else:
+                out.copy_(torch.as_tensor(np.asarray(x0) if isinstance(x0, np.ndarray) else x0).reshape(out.shape))
         s_keep, s_ptr = as_arg(s)
         t_keep, t_ptr = as_arg(t)
         o_keep, o_ptr = as_arg(out)
         info = N.SolveInfo()
-        code = _FORMS[form] | (0 if precond else N.HPS_SOLVE_NO_PRECOND)
+        code = _FORMS[form] | (0 if precond else N.HPS_SOLVE_NO_PRECOND) | (N.HPS_SOLVE_X0 if x0 is not None else 0) \
+            | (0 if graph else N.HPS_SOLVE_NO_GRAPH) | (N.HPS_SOLVE_CGS2 if cgs2 else 0)
         rc = self.lib.hps_gmres_solve(self.handle, code, s_ptr, t_ptr, nrhs, float(tol), o_ptr,
                                       ctypes.byref(info), _stream(stream))
         if rc not in (N.HPS_OK, N.HPS_ENOCONV):
             N.check(rc)
+        if isinstance(out, np.ndarray) and o_keep is not out:
+            out[...] = o_keep
         d = {"iterations": info.iterations, "cycles": info.cycles, "converged": bool(info.converged),
-             "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc}
+             "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc,
+             "reorth_steps": info.reorth_steps}
         return out, d
 
     def recover(self, f, s=None, nrhs=None, stream=None, faces=False):
@@ -224,19 +235,22 @@ class Solver:
         N.check(self.lib.hps_full_precond(self.handle, dt, _ptr(r), _ptr(z), nrhs, _stream(stream)))
         return z
 
-    def full_solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=1, stream=None, precond=True):
+    def full_solve(self, s=None, t=None, tol=1e-10, form="fp64", nrhs=1, stream=None, precond=True, graph=True,
+                   cgs2=False):
         """GMRES on the global system with the per-leaf block-Jacobi preconditioner; returns
         (u, info) with u at every node of every leaf (device complex128)."""
         torch = _torch()
         u = torch.empty(nrhs * self.nl * self.n, dtype=torch.complex128, device="cuda")
         info = N.SolveInfo()
-        f = _FORMS[form] | (0 if precond else N.HPS_SOLVE_NO_PRECOND)
+        f = _FORMS[form] | (0 if precond else N.HPS_SOLVE_NO_PRECOND) | (0 if graph else N.HPS_SOLVE_NO_GRAPH) \
+            | (N.HPS_SOLVE_CGS2 if cgs2 else 0)
         rc = self.lib.hps_full_solve(self.handle, f, _ptr(s), _ptr(t), nrhs, float(tol), _ptr(u), ctypes.byref(info),
                                      _stream(stream))
         if rc not in (0, N.HPS_ENOCONV):
             N.check(rc)
         return u, {"iterations": info.iterations, "cycles": info.cycles, "converged": bool(info.converged),
-                   "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc}
+                   "rel_residual": info.rel_residual, "seconds": info.seconds, "status": rc,
+                   "reorth_steps": info.reorth_steps}
 
     def precond_info(self):
         """(clusters, distinct K_c blocks, distinct B blocks) of the preconditioner."""

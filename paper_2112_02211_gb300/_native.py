@@ -19,6 +19,9 @@ HPS_C64_H16 = 2
 HPS_FORM_FP64 = 1
 HPS_FORM_MIXED = 2
 HPS_SOLVE_NO_PRECOND = 16
+HPS_SOLVE_X0 = 32
+HPS_SOLVE_NO_GRAPH = 64
+HPS_SOLVE_CGS2 = 128
 HPS_PRECOND_NOALLOC_MAX_BYTES = 16 << 20
 HPS_EXPORT_R = 0
 HPS_EXPORT_H = 1
@@ -44,7 +47,7 @@ class Options(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("reorth_steps", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):

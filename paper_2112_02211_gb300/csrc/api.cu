@@ -172,6 +172,16 @@ int check_options(const hps_options& o) {
   return HPS_OK;
 }
 
+constexpr int kSolveFlagBits = HPS_SOLVE_NO_PRECOND | HPS_SOLVE_X0 | HPS_SOLVE_NO_GRAPH | HPS_SOLVE_CGS2;
+
+SolveFlags solve_flags(int form) {
+  SolveFlags f;
+  f.x0 = (form & HPS_SOLVE_X0) != 0;
+  f.no_graph = (form & HPS_SOLVE_NO_GRAPH) != 0;
+  f.cgs2 = (form & HPS_SOLVE_CGS2) != 0;
+  return f;
+}
+
 int check_finite(const double* v, long long n, const char* what) {
   for (long long i = 0; i < n; ++i)
     if (!std::isfinite(v[i])) {
@@ -485,7 +495,8 @@ int hps_full_solve(hps_handle* h, int form, const double* s, const double* t, in
     return HPS_EINVAL;
   }
   const bool no_pc = (form & HPS_SOLVE_NO_PRECOND) != 0;
-  form &= ~HPS_SOLVE_NO_PRECOND;
+  const SolveFlags fl = solve_flags(form);
+  form &= ~kSolveFlagBits;
   if (form != HPS_FORM_FP64 && form != HPS_FORM_MIXED) {
     set_error("hps_full_solve: form must be HPS_FORM_FP64 or HPS_FORM_MIXED");
     return HPS_EINVAL;
@@ -512,7 +523,7 @@ int hps_full_solve(hps_handle* h, int form, const double* s, const double* t, in
   HPS_CUDA_TRY(cudaSetDevice(h->dev));
   cudaStream_t st = (cudaStream_t)stream;
   const auto t0 = std::chrono::steady_clock::now();
-  int rc = full_solve(h, form, !no_pc, (const double2*)s, (const double2*)t, nrhs, tol, (double2*)u_out, info, st);
+  int rc = full_solve(h, form, !no_pc, (const double2*)s, (const double2*)t, nrhs, tol, (double2*)u_out, info, st, fl);
   HPS_CUDA_TRY(cudaStreamSynchronize(st));
   if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return rc;
@@ -578,7 +589,8 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
     return HPS_EINVAL;
   }
   const bool no_pc = (form & HPS_SOLVE_NO_PRECOND) != 0;
-  form &= ~HPS_SOLVE_NO_PRECOND;
+  const SolveFlags fl = solve_flags(form);
+  form &= ~kSolveFlagBits;
   if (form != HPS_FORM_FP64 && form != HPS_FORM_MIXED) {
     set_error("hps_gmres_solve: form must be HPS_FORM_FP64 or HPS_FORM_MIXED");
     return HPS_EINVAL;
@@ -626,7 +638,11 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
   }
   const bool fdev = is_device_ptr(f_out);
   double2* x = fdev ? (double2*)f_out : k.x;
-  rc = gmres_solve(h, form, k.b, x, nrhs, tol, info, st, !no_pc);
+  if (fl.x0 && !fdev) {
+    if ((rc = check_finite(f_out, 2LL * nrhs * h->nf, "initial guess"))) return rc;
+    HPS_CUDA_TRY(cudaMemcpyAsync(x, f_out, (size_t)nrhs * h->nf * sizeof(double2), cudaMemcpyHostToDevice, st));
+  }
+  rc = gmres_solve(h, form, k.b, x, nrhs, tol, info, st, !no_pc, fl);
   if (rc != HPS_OK && rc != HPS_ENOCONV) return rc;
   if (!fdev) {
     HPS_CUDA_TRY(cudaMemcpyAsync(f_out, x, (size_t)nrhs * h->nf * sizeof(double2), cudaMemcpyDeviceToHost, st));

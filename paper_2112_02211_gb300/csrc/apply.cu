@@ -273,8 +273,12 @@ struct PrecKP {
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
+// gate: while a GMRES cycle is replayed from a graph, the word that says whether any
+// right-hand side is still active (0: return at once); nullptr otherwise.
 template <class P, int NR, int RPW>
-__global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Args A, int xcap, int rowcap) {
+__global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Args A, int xcap, int rowcap,
+                                                            const int* gate) {
+  if (gate && *gate == 0) return;
   using TM = typename P::TM;
   using Acc = typename P::Acc;
   constexpr int VPL = MT<TM>::VPL;
@@ -364,6 +368,7 @@ struct PrecBArgs {
   const TIN* r;
   TOUT* z;
   TOUT* t;
+  const int* gate;  // as in seg_gemv_kernel
 };
 
 template <class TM> __device__ __forceinline__ typename MT<TM>::Acc load_one(const TM* p);
@@ -373,6 +378,7 @@ template <> __device__ __forceinline__ double2 load_one<double2>(const double2* 
 
 template <class TM, class TIN, class TOUT>
 __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TIN, TOUT> A) {
+  if (A.gate && *A.gate == 0) return;
   using Acc = typename MT<TM>::Acc;
   extern __shared__ __align__(16) unsigned char smraw[];
   Acc* xs = reinterpret_cast<Acc*>(smraw);  // 6 q^2
@@ -406,7 +412,8 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
 }
 
 template <class P, int NR, int RPW>
-cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm, cudaStream_t st, long long* counter) {
+cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm, cudaStream_t st, long long* counter,
+                       const int* gate) {
   using Acc = typename P::Acc;
   const size_t smem = ((size_t)NR * xcap + (size_t)NR * rowcap) * sizeof(Acc);
   auto kern = seg_gemv_kernel<P, NR, RPW>;
@@ -418,7 +425,7 @@ cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm,
   occ = std::max(occ, 1);
   long long grid = std::min<long long>(A.nitems, (long long)nsm * occ);
   if (grid <= 0) return cudaSuccess;
-  kern<<<(unsigned)grid, kThreads, smem, st>>>(A, xcap, rowcap);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(A, xcap, rowcap, gate);
   ++*counter;
   return cudaGetLastError();
 }
@@ -435,10 +442,10 @@ cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int
     shift(B, r0);
     B.nrhs = nr;
     cudaError_t e;
-    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, rowcap, nsm, st, counter);
-    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, rowcap, nsm, st, counter);
-    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, rowcap, nsm, st, counter);
-    else e = launch_one<P, 8, 1>(B, xcap, rowcap, nsm, st, counter);
+    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, rowcap, nsm, st, counter, h->gate);
+    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, rowcap, nsm, st, counter, h->gate);
+    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, rowcap, nsm, st, counter, h->gate);
+    else e = launch_one<P, 8, 1>(B, xcap, rowcap, nsm, st, counter, h->gate);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -492,6 +499,7 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.bsc = h->dct.bsc;
     A.nl = h->nl;
     A.q2 = q2;
+    A.gate = h->gate;
     using Acc = typename MT<TM>::Acc;
     const size_t smem = (size_t)h->nb * sizeof(Acc);
     auto kern = prec_b_kernel<TM, TIN, TOUT>;
@@ -546,10 +554,10 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
         A.items = h->dct.kitems[g];
         A.nitems = n;
         A.nrhs = 1 << g;
-        if (g == 0) e = launch_one<P, 1, 4>(A, xcap, q2, h->nsm, st, counter);
-        else if (g == 1) e = launch_one<P, 2, 4>(A, xcap, q2, h->nsm, st, counter);
-        else if (g == 2) e = launch_one<P, 4, 2>(A, xcap, q2, h->nsm, st, counter);
-        else e = launch_one<P, 8, 2>(A, xcap, q2, h->nsm, st, counter);
+        if (g == 0) e = launch_one<P, 1, 4>(A, xcap, q2, h->nsm, st, counter, h->gate);
+        else if (g == 1) e = launch_one<P, 2, 4>(A, xcap, q2, h->nsm, st, counter, h->gate);
+        else if (g == 2) e = launch_one<P, 4, 2>(A, xcap, q2, h->nsm, st, counter, h->gate);
+        else e = launch_one<P, 8, 2>(A, xcap, q2, h->nsm, st, counter, h->gate);
       }
     }
     h->prof.end(HPS_PHASE_PRECOND_K, ev, st);

@@ -86,10 +86,12 @@ struct FullApplyArgs {
   const double2* b;  // residual mode: y = b - A u
   long long nu;      // values per right-hand side
   int nrhs;
+  const int* gate;   // while a GMRES cycle is replayed: 0 = return at once
 };
 
 template <class R, class TIN, class TOUT>
 __global__ void __launch_bounds__(kFT) full_apply_kernel(FullApplyArgs a) {
+  if (a.gate && *a.gate == 0) return;
   using C = typename Cx<R>::T;
   const int p = a.G.p, n1 = a.G.n1, ni = a.G.ni, n = a.G.n;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -231,10 +233,12 @@ struct FullPrecArgs {
   void* z;
   long long nu;
   int nrhs;
+  const int* gate;   // as in FullApplyArgs
 };
 
 template <class R, class TS, class TIN, class TOUT>
 __global__ void __launch_bounds__(kFT) full_precond_kernel(FullPrecArgs a) {
+  if (a.gate && *a.gate == 0) return;
   using C = typename Cx<R>::T;
   const int p = a.G.p, n1 = a.G.n1, ni = a.G.ni, nb = a.G.nb, n = a.G.n;
   const int pa = 2 * n1 * n1 + n1;
@@ -370,6 +374,7 @@ cudaError_t full_apply_t(const hps_handle* h, const void* u, void* y, const doub
   a.b = b;
   a.nu = (long long)h->nl * h->n;
   a.nrhs = nrhs;
+  a.gate = h->gate;
   const size_t smem = (size_t)h->n * sizeof(C) + (size_t)6 * h->p * h->p * sizeof(R);
   auto kern = full_apply_kernel<R, TIN, TOUT>;
   cudaError_t e = allow_dynamic_smem((const void*)kern, smem);
@@ -400,6 +405,7 @@ cudaError_t full_precond_t(const hps_handle* h, const TS* S, const void* r, void
   a.z = z;
   a.nu = (long long)h->nl * h->n;
   a.nrhs = nrhs;
+  a.gate = h->gate;
   const int pa = 2 * h->n1 * h->n1 + h->n1;
   const size_t smem =
       (size_t)(h->n + 3 * h->ni + 2 * h->nb) * sizeof(C) + (size_t)(6 * h->p * h->p + 3 * pa) * sizeof(R);
@@ -453,7 +459,7 @@ cudaError_t launch_full_precond(const hps_handle* h, bool fp64, VType tin, const
 // restart).  s: nrhs interior vectors or NULL, t: nrhs face vectors at Gauss
 // points or NULL, u: nrhs global vectors (device).
 int full_solve(hps_handle* h, int form, bool use_precond, const double2* s, const double2* t, int nrhs, double tol,
-               double2* u, hps_solve_info* info, cudaStream_t st) {
+               double2* u, hps_solve_info* info, cudaStream_t st, SolveFlags fl) {
   const bool mixed = (form == HPS_FORM_MIXED);
   const long long nu = (long long)h->nl * h->n;
   int rc = krylov_alloc(h, nrhs, nu);
@@ -483,7 +489,8 @@ int full_solve(hps_handle* h, int form, bool use_precond, const double2* s, cons
     h->prof.end(HPS_PHASE_RESIDUAL, ev, s2);
     return e;
   };
-  return gmres_core(h, ops, mixed, h->ks.b, u, nrhs, tol, info, st);
+  ops.id = 1;
+  return gmres_core(h, ops, mixed, h->ks.b, u, nrhs, tol, info, st, fl);
 }
 
 }  // namespace hps

@@ -132,15 +132,20 @@ struct DeviceClusterTables {
   int* bsc = nullptr;
 };
 
-// Per-phase CUDA-event timing and a launch counter (see hps_profile).
+// Per-phase CUDA-event timing and a launch counter (see hps_profile).  Events
+// are recorded as external events, so an interval recorded while a stream is
+// being captured becomes a pair of event nodes of the graph; such intervals
+// are taken out with take_recs() and read after every replay (read_recs).
 struct Profiler {
   bool on = false;
   long long launches = 0;
   double ms[HPS_NPHASES] = {};
   long long count[HPS_NPHASES] = {};
+  int step = -1;  // Arnoldi step the next intervals belong to (-1: none)
   struct Rec {
     int phase;
     cudaEvent_t a, b;
+    int step;
   };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> recs;
@@ -158,14 +163,40 @@ struct Profiler {
   cudaEvent_t begin(cudaStream_t st) {
     if (!on) return nullptr;
     cudaEvent_t e = take();
-    cudaEventRecord(e, st);
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
     return e;
   }
   void end(int phase, cudaEvent_t a, cudaStream_t st) {
     if (!on || !a) return;
     cudaEvent_t e = take();
-    cudaEventRecord(e, st);
-    recs.push_back({phase, a, e});
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    recs.push_back({phase, a, e, step});
+  }
+  // Intervals recorded since `from` (into a graph being captured); their events now
+  // belong to the caller.
+  std::vector<Rec> take_recs(size_t from) {
+    std::vector<Rec> out(recs.begin() + from, recs.end());
+    recs.resize(from);
+    return out;
+  }
+  // Adds the intervals of one replay of a graph, those of steps < steps_done (and those
+  // outside the steps) only.
+  void read_recs(const std::vector<Rec>& rs, int steps_done) {
+    for (const Rec& r : rs) {
+      if (r.step >= steps_done) continue;
+      float t = 0.f;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.phase] += t;
+      count[r.phase] += 1;
+    }
+  }
+  void release(std::vector<Rec>& rs) {
+    for (const Rec& r : rs) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    rs.clear();
   }
   void flush() {
     for (const Rec& r : recs) {
@@ -207,6 +238,19 @@ struct FullSystem {
   double* eig = nullptr;     // 3 x (2 n1^2 + n1)
 };
 
+// One restart cycle of GMRES (the first basis vector and m Arnoldi steps)
+// captured as a CUDA graph; replayed every cycle of every solve with the same
+// configuration.  Steps after convergence find the device gate closed and exit.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  // what the captured launches depend on
+  int nrhs = 0, m = 0, ops_id = -1, mixed = 0, pc = 0, c64op = 0, cgs2 = 0, prof = 0;
+  long long n = 0;
+  const void* V = nullptr;
+  long long launches = 0;                 // kernels per replay
+  std::vector<Profiler::Rec> recs;        // timed intervals inside the graph
+};
+
 struct KrylovSpace {
   int m = 0, nrhs = 0, nblk = 0;
   long long nf = 0;
@@ -226,11 +270,12 @@ struct KrylovSpace {
   double2* y = nullptr;      // nrhs x m
   double* est = nullptr;     // nrhs: |g_{j+1}| after the last step
   double* nrm = nullptr;     // nrhs: norms
-  int* active = nullptr;     // nrhs
+  int* active = nullptr;     // nrhs; then kcount[nrhs], any_active, status, reorth[nrhs], nreorth
   int* status = nullptr;     // device status word (breakdown etc.)
   double2* s_dev = nullptr;  // staging for host inputs
   double2* t_dev = nullptr;
   double2* f_dev = nullptr;
+  CycleGraph graph;
   size_t bytes = 0;
 };
 
@@ -276,6 +321,10 @@ struct hps_handle {
   void* pc_scratch = nullptr;  // nslots*q^2*max_rhs complex double (precond t buffer)
 
   int* tc_error = nullptr;  // device error word of the tensor-core kernels
+  // While a GMRES cycle is captured: the device word that the per-step kernels
+  // (apply, preconditioner) read first, returning at once when it is 0 (no
+  // right-hand side still active).  nullptr otherwise.
+  mutable const int* gate = nullptr;
   hps::KrylovSpace ks;
   mutable hps::Profiler prof;
   size_t bytes = 0;
@@ -363,12 +412,19 @@ struct GmresOps {
   // mixed form without a preconditioner: the apply takes the basis vector rounded to complex
   // FP32 (kept beside the double-float basis) instead of the double-float vector itself
   bool c64_operand = false;
+  int id = 0;  // which operator family (face system 0, global system 1): part of the graph key
+};
+// Solve flags of gmres_core (bits of hps_gmres_solve's form beyond the form itself).
+struct SolveFlags {
+  bool x0 = false;       // x holds an initial guess
+  bool no_graph = false; // launch the Arnoldi steps one by one instead of replaying a graph
+  bool cgs2 = false;     // always two Gram-Schmidt passes (else the second only when needed)
 };
 int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b, double2* x, int nrhs, double tol,
-               hps_solve_info* info, cudaStream_t st);
+               hps_solve_info* info, cudaStream_t st, SolveFlags fl = SolveFlags());
 int full_solve(hps_handle* h, int form, bool use_precond, const double2* s, const double2* t, int nrhs, double tol,
-               double2* u, hps_solve_info* info, cudaStream_t st);
+               double2* u, hps_solve_info* info, cudaStream_t st, SolveFlags fl = SolveFlags());
 int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol,
-                hps_solve_info* info, cudaStream_t st, bool use_precond);
+                hps_solve_info* info, cudaStream_t st, bool use_precond, SolveFlags fl = SolveFlags());
 
 }  // namespace hps

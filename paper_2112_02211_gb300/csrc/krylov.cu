@@ -64,6 +64,7 @@ struct VecArgs {
   const double2* coef;  // [rhs][cstride]
   int cstride;
   const int* active;
+  int self_dot;      // mdot: also w^H w (= ||w||^2) in slot nvec
 };
 
 // part = block partials of V_{0..nvec-1}^H w
@@ -79,15 +80,16 @@ __global__ void __launch_bounds__(kT) mdot_kernel(VecArgs a) {
     wv[e] = (i < a.nf) ? w[i] : make_double2(0.0, 0.0);
   }
   double2* out = a.part + ((long long)rhs * a.nblk + blk) * a.M1;
-  for (int g0 = 0; g0 < a.nvec; g0 += kG) {
-    const int ng = min(kG, a.nvec - g0);
+  const int nv = a.nvec + a.self_dot;
+  for (int g0 = 0; g0 < nv; g0 += kG) {
+    const int ng = min(kG, nv - g0);
     double2 acc[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) acc[g] = make_double2(0.0, 0.0);
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
       if (g < ng) {
-        const double2* v = a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf;
+        const double2* v = (g0 + g < a.nvec) ? a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf : w;
 #pragma unroll
         for (int e = 0; e < kE; ++e) {
           const long long i = base + (long long)e * kT;
@@ -185,6 +187,7 @@ struct DfArgs {
   const double2* coef;
   int cstride;
   const int* active;
+  int self_dot;     // mdot: also w^H w (= ||w||^2) in slot nvec
 };
 
 // Compensated accumulation in the spirit of Ogita, Rump and Oishi's Dot2:
@@ -278,20 +281,23 @@ __device__ __forceinline__ dfc warp_reduce_groups(const dfc (&part)[kG]) {
   return k;
 }
 
-// Partial dots V^H w of this block (one per basis vector, complex double): per group of kG
-// vectors each warp reduces its lanes' partials on its own; one barrier at the end sums the
-// warps in order.  nvec <= 64 (restart <= 60).
-__device__ __forceinline__ void df_dots(const DfArgs& a, int rhs, long long base, const dfc (&wv)[kE], double2* out) {
+// Partial dots V^H w of this block (one per basis vector, complex double; with nv = nvec + 1
+// the last "basis vector" is w itself, giving ||w||^2): per group of kG vectors each warp
+// reduces its lanes' partials on its own; one barrier at the end sums the warps in order.
+// nv <= 64 (restart <= 60).
+__device__ __forceinline__ void df_dots(const DfArgs& a, int rhs, long long base, const dfc (&wv)[kE], double2* out,
+                                        int nv) {
   __shared__ dfc wred[kT / 32][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int g0 = 0; g0 < a.nvec; g0 += kG) {
-    const int ng = min(kG, a.nvec - g0);
+  for (int g0 = 0; g0 < nv; g0 += kG) {
+    const int ng = min(kG, nv - g0);
     dfc part[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
       acc2 re{0.f, 0.f}, im{0.f, 0.f};
       if (g < ng) {
-        const float4* v = a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf;
+        const float4* v = (g0 + g < a.nvec) ? a.V + ((long long)(g0 + g) * a.nrhs + rhs) * a.nf
+                                            : a.w + (long long)rhs * a.nf;
         float4 vv[kE];
 #pragma unroll
         for (int e = 0; e < kE; ++e) {
@@ -307,7 +313,7 @@ __device__ __forceinline__ void df_dots(const DfArgs& a, int rhs, long long base
     if ((lane & 7) == 0 && (lane >> 3) < ng) wred[warp][g0 + (lane >> 3)] = sum;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < a.nvec; j += kT) {
+  for (int j = threadIdx.x; j < nv; j += kT) {
     dfc t = wred[0][j];
 #pragma unroll
     for (int w = 1; w < kT / 32; ++w) t = dfc_add(t, wred[w][j]);
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(kT, 4) mdot_df_kernel(DfArgs a) {
     const long long i = base + (long long)e * kT;
     wv[e] = (i < a.nf) ? dfc_load(w[i]) : dfc_zero();
   }
-  df_dots(a, rhs, base, wv, a.part + ((long long)rhs * a.nblk + blk) * a.M1);
+  df_dots(a, rhs, base, wv, a.part + ((long long)rhs * a.nblk + blk) * a.M1, a.nvec + a.self_dot);
 }
 
 // w -= V coef; then (mode 1) partial dots V^H w, or (mode 2) partial ||w||^2.
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(kT, 4) axpy_df_kernel(DfArgs a, int mode) {
   }
   double2* out = a.part + ((long long)rhs * a.nblk + blk) * a.M1;
   if (mode == 1) {
-    df_dots(a, rhs, base, wv, out);
+    df_dots(a, rhs, base, wv, out, a.nvec);
   } else if (mode == 2) {
     dfc part[kG];
 #pragma unroll
@@ -393,8 +399,9 @@ __global__ void __launch_bounds__(kT, 4) axpy_df_kernel(DfArgs a, int mode) {
 
 // w <- w * invn[rhs] in double-float; c32 (if given) receives the result rounded to complex FP32
 // (the normalized double-float's high part), the operand of the tensor-core apply
-__global__ void scale_df_kernel(float4* w, long long nf, const double* invn, float2* c32) {
+__global__ void scale_df_kernel(float4* w, long long nf, const double* invn, float2* c32, const int* active) {
   const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
   const dfr s = df_from_double(invn[rhs]);
   float4* p = w + rhs * nf;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
@@ -416,9 +423,11 @@ __global__ void scale_copy_df_kernel(const double2* src, float4* dst, long long 
   }
 }
 
-// u (complex double) = sum_{j<kmax} y_j v_j, accumulated in double-float
-__global__ void combine_df_kernel(const float4* V, int nrhs, long long nf, int kmax, int m, const double2* y, double2* u) {
+// u (complex double) = sum_{j<kmax} y_j v_j, accumulated in double-float; kmax = kcount[rhs]
+__global__ void combine_df_kernel(const float4* V, int nrhs, long long nf, const int* kcount, int m, const double2* y,
+                                  double2* u) {
   const int rhs = blockIdx.y;
+  const int kmax = kcount[rhs];
   __shared__ dfc ys[64];
   for (int j = threadIdx.x; j < kmax; j += blockDim.x) ys[j] = dfc_from(y[(long long)rhs * m + j]);
   __syncthreads();
@@ -571,9 +580,11 @@ __global__ void lsq_kernel(int nrhs, int m, int M1, const double2* H, const doub
   }
 }
 
-// u = sum_{j<kmax} y_j v_j
-__global__ void combine_kernel(const double2* V, int nrhs, long long nf, int kmax, int m, const double2* y, double2* u) {
+// u = sum_{j<kmax} y_j v_j, kmax = kcount[rhs]
+__global__ void combine_kernel(const double2* V, int nrhs, long long nf, const int* kcount, int m, const double2* y,
+                               double2* u) {
   const int rhs = blockIdx.y;
+  const int kmax = kcount[rhs];
   __shared__ double2 ys[64];
   for (int j = threadIdx.x; j < kmax; j += blockDim.x) ys[j] = y[(long long)rhs * m + j];
   __syncthreads();
@@ -591,6 +602,24 @@ template <class T>
 __global__ void xpy_kernel(double2* x, const T* z, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] = cadd(x[i], cvt<double2>(z[i]));
+}
+
+// Second Gram-Schmidt pass only where needed (the criterion of Daniel, Gragg, Kaufman and
+// Stewart, 1976): after one classical pass w' = w - V h, reorthogonalize when
+// ||w'|| < ||w|| / sqrt(2), i.e. when the pass removed more than half of w's energy and
+// cancellation may have left w' visibly non-orthogonal to V.  hcol[j+1] holds ||w||^2 (from
+// the first dot pass), hcol[M1] ||w'||^2.  Steps that skip the second pass get h2 = 0.
+__global__ void dgks_kernel(int nrhs, int j, int M1, const double2* hcol, const int* active, int* reorth, double2* h2,
+                            int* nreorth) {
+  const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= nrhs) return;
+  const double2* hc = hcol + (long long)rhs * (M1 + 1);
+  const bool act = active[rhs] != 0;
+  const bool need = act && hc[M1].x < 0.5 * hc[j + 1].x;
+  reorth[rhs] = need ? 1 : 0;
+  if (need) atomicAdd(nreorth, 1);
+  else if (act)
+    for (int t = 0; t <= j; ++t) h2[(long long)rhs * M1 + t] = make_double2(0.0, 0.0);
 }
 
 // norms[rhs] = ||x_rhs||_2 from block partials
@@ -619,8 +648,6 @@ __global__ void norm_final_kernel(const double* part, int nblk, int nrhs, double
   for (int b = 0; b < nblk; ++b) s += part[(long long)rhs * nblk + b];
   out[rhs] = sqrt(s);
 }
-
-struct Flt {};
 
 }  // namespace
 
@@ -671,13 +698,24 @@ int krylov_alloc(hps_handle* h, int nrhs, long long nvec) {
   if ((rc = alloc((void**)&k.g, (size_t)nrhs * M1 * sizeof(double2)))) return rc;
   if ((rc = alloc((void**)&k.est, (size_t)nrhs * 4 * sizeof(double)))) return rc;  // est, invn, target, norms
   if ((rc = alloc((void**)&k.nrm, (size_t)nrhs * std::max(256, k.nblk) * sizeof(double)))) return rc;
-  if ((rc = alloc((void**)&k.active, (size_t)(2 * nrhs + 2) * sizeof(int)))) return rc;  // active, kcount, any, status
+  // active[nrhs], kcount[nrhs], any_active, status, reorth[nrhs], nreorth
+  if ((rc = alloc((void**)&k.active, (size_t)(3 * nrhs + 3) * sizeof(int)))) return rc;
   k.status = k.active + 2 * nrhs + 1;
   k.bytes = total;
   return HPS_OK;
 }
 
+namespace {
+void destroy_graph(hps_handle* h) {
+  CycleGraph& g = h->ks.graph;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->prof.release(g.recs);
+  g = CycleGraph();
+}
+}  // namespace
+
 void krylov_free(hps_handle* h) {
+  destroy_graph(h);
   h->prof.destroy();
   KrylovSpace& k = h->ks;
   void* ptrs[] = {k.V, k.x, k.r, k.b, k.u, k.z, k.zt, k.part, k.hcol, k.y, k.H, k.cs, k.sn, k.g, k.est, k.nrm, k.active,
@@ -689,7 +727,10 @@ void krylov_free(hps_handle* h) {
 
 namespace {
 
-int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& out, cudaStream_t st) {
+// ||x_rhs|| of every right-hand side into out (host); also copies n_ints ints from dev_ints
+// (when given) in the same synchronization.
+int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& out, cudaStream_t st,
+              const int* dev_ints = nullptr, int* host_ints = nullptr, int n_ints = 0) {
   KrylovSpace& k = h->ks;
   const int nblk = 256;
   double* part = k.nrm;
@@ -701,14 +742,22 @@ int vec_norms(hps_handle* h, const double2* x, int nrhs, std::vector<double>& ou
   h->prof.launches += 2;
   out.resize(nrhs);
   HPS_CUDA_TRY(cudaMemcpyAsync(out.data(), res, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (dev_ints)
+    HPS_CUDA_TRY(cudaMemcpyAsync(host_ints, dev_ints, n_ints * sizeof(int), cudaMemcpyDeviceToHost, st));
   HPS_CUDA_TRY(cudaStreamSynchronize(st));
   return HPS_OK;
 }
 
 }  // namespace
 
+// Restarted GMRES (right preconditioning) with the operators of `ops`.  Per restart cycle:
+// the host sets the per-RHS targets, then the first basis vector and up to m Arnoldi steps run
+// on the device without any host synchronization -- replayed from a CUDA graph captured once
+// per configuration, in which every kernel of step j + 1 returns at once when step j left no
+// right-hand side active (device gate) -- then x += M^{-1} V y and the FP64 true residual,
+// whose norms (and the step counts) are the cycle's one read-back.
 int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b, double2* x, int nrhs, double tol,
-               hps_solve_info* info, cudaStream_t st) {
+               hps_solve_info* info, cudaStream_t st, SolveFlags fl) {
   const auto t0 = std::chrono::steady_clock::now();
   int rc = krylov_alloc(h, nrhs, ops.n);
   if (rc) return rc;
@@ -722,21 +771,153 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
   int* active = k.active;
   int* kcount = k.active + nrhs;
   int* any_active = k.active + 2 * nrhs;
+  int* reorth = k.active + 2 * nrhs + 2;
+  int* nreorth = k.active + 3 * nrhs + 2;
   double2* h2 = k.y;  // pass-2 coefficients reuse the y buffer until the cycle ends
   const int gblk = std::min<long long>(4 * h->nsm, (nf + 255) / 256);
   const dim3 vgrid(gblk, nrhs);
+  const bool pc = ops.pc;
+  const bool cgs2 = fl.cgs2;
+  // unpreconditioned mixed form with a complex-FP32 operand: v_j is also kept rounded in z
+  float2* vc32 = (mixed && !pc && ops.c64_operand) ? (float2*)k.z : nullptr;
+
+  // first basis vector of the cycle: v_0 = r / ||r||
+  auto first_vector = [&](cudaStream_t s) -> int {
+    if (mixed)
+      scale_copy_df_kernel<<<vgrid, 256, 0, s>>>(k.r, (float4*)k.V, nf, invn, vc32);
+    else
+      scale_copy_kernel<<<vgrid, 256, 0, s>>>(k.r, k.V, nf, invn);
+    HPS_CUDA_TRY(cudaGetLastError());
+    h->prof.launches += 1;
+    return HPS_OK;
+  };
+  // Arnoldi step j: w = A M^{-1} v_j, orthogonalized against v_0..v_j, the Hessenberg
+  // column rotated, v_{j+1} = w / h_{j+1,j}
+  auto step = [&](int j, cudaStream_t s) -> int {
+    h->prof.step = j;
+    double2* vj = k.V + (long long)j * nrhs * nf;
+    double2* w = k.V + (long long)(j + 1) * nrhs * nf;
+    const VType vt = mixed ? VType::DF : VType::C128, zt = mixed ? VType::C64 : VType::C128;
+    if (pc) {
+      HPS_CUDA_TRY(ops.precond(vt, vj, zt, k.z, nrhs, s));
+      HPS_CUDA_TRY(ops.apply(zt, k.z, vt, w, nrhs, s));
+    } else if (vc32) {
+      HPS_CUDA_TRY(ops.apply(VType::C64, vc32, vt, w, nrhs, s));
+    } else {
+      HPS_CUDA_TRY(ops.apply(vt, vj, vt, w, nrhs, s));
+    }
+    VecArgs va;
+    va.V = k.V;
+    va.w = w;
+    va.nf = nf;
+    va.nrhs = nrhs;
+    va.nvec = j + 1;
+    va.M1 = M1;
+    va.nblk = k.nblk;
+    va.part = k.part;
+    va.active = active;
+    va.self_dot = 0;
+    DfArgs da;
+    da.V = (const float4*)k.V;
+    da.w = (float4*)w;
+    da.nf = nf;
+    da.nrhs = nrhs;
+    da.nvec = j + 1;
+    da.M1 = M1;
+    da.nblk = k.nblk;
+    da.part = k.part;
+    da.active = active;
+    da.self_dot = 0;
+    const dim3 bgrid(k.nblk, nrhs);
+    auto mdot = [&](const int* act, int self) {
+      va.active = da.active = act;
+      va.self_dot = da.self_dot = self;
+      if (mixed) mdot_df_kernel<<<bgrid, kT, 0, s>>>(da);
+      else mdot_kernel<<<bgrid, kT, 0, s>>>(va);
+      va.self_dot = da.self_dot = 0;
+    };
+    auto axpy = [&](const int* act, const double2* coef, int cstride, int mode) {
+      va.active = da.active = act;
+      va.coef = da.coef = coef;
+      va.cstride = da.cstride = cstride;
+      if (mixed) axpy_df_kernel<<<bgrid, kT, 0, s>>>(da, mode);
+      else axpy_kernel<<<bgrid, kT, 0, s>>>(va, mode);
+    };
+    auto reduce = [&](int n, double2* out, int ostride, const int* act) {
+      reduce_kernel<<<dim3(n, nrhs), kT, 0, s>>>(k.part, k.nblk, M1, out, ostride, 0, act);
+    };
+    cudaEvent_t ev_arn = h->prof.begin(s);
+    if (cgs2) {
+      // classical Gram-Schmidt twice: dots; update + dots; update + norm
+      mdot(active, 0);
+      reduce(j + 1, k.hcol, M1 + 1, active);
+      axpy(active, k.hcol, M1 + 1, 1);
+      reduce(j + 1, h2, M1, active);
+      axpy(active, h2, M1, 2);
+      reduce(1, k.hcol + M1, M1 + 1, active);
+      h->prof.launches += 6;
+    } else {
+      // one pass (dots and ||w||^2; update + norm), the second only where the DGKS test asks
+      mdot(active, 1);
+      reduce(j + 2, k.hcol, M1 + 1, active);
+      axpy(active, k.hcol, M1 + 1, 2);
+      reduce(1, k.hcol + M1, M1 + 1, active);
+      dgks_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(nrhs, j, M1, k.hcol, active, reorth, h2, nreorth);
+      mdot(reorth, 0);
+      reduce(j + 1, h2, M1, reorth);
+      axpy(reorth, h2, M1, 2);
+      reduce(1, k.hcol + M1, M1 + 1, reorth);
+      h->prof.launches += 9;
+    }
+    HPS_CUDA_TRY(cudaGetLastError());
+    HPS_CUDA_TRY(cudaMemsetAsync(any_active, 0, sizeof(int), s));
+    GivensArgs ga;
+    ga.nrhs = nrhs;
+    ga.m = m;
+    ga.j = j;
+    ga.M1 = M1;
+    ga.nblk = k.nblk;
+    ga.part = k.part;
+    ga.hcol = k.hcol;
+    ga.h2 = h2;
+    ga.H = k.H;
+    ga.cs = k.cs;
+    ga.sn = k.sn;
+    ga.g = k.g;
+    ga.est = est;
+    ga.invn = invn;
+    ga.active = active;
+    ga.kcount = kcount;
+    ga.target = target;
+    ga.any_active = any_active;
+    givens_kernel<<<nrhs, 64, 0, s>>>(ga);
+    HPS_CUDA_TRY(cudaGetLastError());
+    if (mixed) scale_df_kernel<<<vgrid, 256, 0, s>>>((float4*)w, nf, invn, vc32, active);
+    else scale_kernel<<<vgrid, 256, 0, s>>>(w, nf, nrhs, invn, active);
+    HPS_CUDA_TRY(cudaGetLastError());
+    h->prof.end(HPS_PHASE_ARNOLDI, ev_arn, s);
+    h->prof.launches += 2;
+    h->prof.step = -1;
+    return HPS_OK;
+  };
 
   std::vector<double> bnorm, rnorm;
   if ((rc = vec_norms(h, b, nrhs, bnorm, st))) return rc;
-  HPS_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
-  HPS_CUDA_TRY(cudaMemcpyAsync(k.r, b, vb, cudaMemcpyDeviceToDevice, st));
-  rnorm = bnorm;
+  if (fl.x0) {
+    HPS_CUDA_TRY(ops.residual(x, b, k.r, nrhs, st));
+    if ((rc = vec_norms(h, k.r, nrhs, rnorm, st))) return rc;
+  } else {
+    HPS_CUDA_TRY(cudaMemsetAsync(x, 0, vb, st));
+    HPS_CUDA_TRY(cudaMemcpyAsync(k.r, b, vb, cudaMemcpyDeviceToDevice, st));
+    rnorm = bnorm;
+  }
   int its = 0, cycles = 0;
+  long long nre_total = 0;
   const double eps_inner = mixed ? 1e-6 : 0.0;
   std::vector<double> htarget(nrhs), hinv(nrhs);
-  std::vector<int> hact(nrhs);
+  std::vector<int> hints(2 * nrhs + 1), hread(3 * nrhs + 3);
+  std::vector<double2> g0((size_t)nrhs * M1);
   bool converged = false;
-  const bool pc = ops.pc;
   while (true) {
     bool all = true;
     for (int r = 0; r < nrhs; ++r)
@@ -746,127 +927,92 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
       break;
     }
     if (its >= h->opt.maxit) break;
+    std::fill(hints.begin(), hints.end(), 0);
+    std::fill(g0.begin(), g0.end(), make_double2(0.0, 0.0));
     for (int r = 0; r < nrhs; ++r) {
       const bool act = bnorm[r] > 0.0 && rnorm[r] > tol * bnorm[r];
-      hact[r] = act ? 1 : 0;
+      hints[r] = act ? 1 : 0;  // active; kcount stays 0
       htarget[r] = std::max(0.5 * tol * bnorm[r], eps_inner * rnorm[r]);
       hinv[r] = act ? 1.0 / rnorm[r] : 0.0;
+      g0[(size_t)r * M1] = make_double2(act ? rnorm[r] : 0.0, 0.0);
     }
-    HPS_CUDA_TRY(cudaMemcpyAsync(active, hact.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    hints[2 * nrhs] = 1;  // any_active: the first step runs
+    HPS_CUDA_TRY(cudaMemcpyAsync(active, hints.data(), hints.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    HPS_CUDA_TRY(cudaMemsetAsync(nreorth, 0, sizeof(int), st));
     HPS_CUDA_TRY(cudaMemcpyAsync(target, htarget.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
     HPS_CUDA_TRY(cudaMemcpyAsync(invn, hinv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-    HPS_CUDA_TRY(cudaMemsetAsync(kcount, 0, nrhs * sizeof(int), st));
-    HPS_CUDA_TRY(cudaMemsetAsync(k.g, 0, (size_t)nrhs * M1 * sizeof(double2), st));
-    {
-      std::vector<double2> g0(nrhs);
-      for (int r = 0; r < nrhs; ++r) g0[r] = make_double2(hact[r] ? rnorm[r] : 0.0, 0.0);
-      for (int r = 0; r < nrhs; ++r)
-        HPS_CUDA_TRY(cudaMemcpyAsync(k.g + (long long)r * M1, &g0[r], sizeof(double2), cudaMemcpyHostToDevice, st));
-      HPS_CUDA_TRY(cudaStreamSynchronize(st));
-    }
-    // unpreconditioned mixed form with a complex-FP32 operand: v_j is also kept rounded in z
-    float2* vc32 = (mixed && !pc && ops.c64_operand) ? (float2*)k.z : nullptr;
-    if (mixed)
-      scale_copy_df_kernel<<<vgrid, 256, 0, st>>>(k.r, (float4*)k.V, nf, invn, vc32);
-    else
-      scale_copy_kernel<<<vgrid, 256, 0, st>>>(k.r, k.V, nf, invn);
-    HPS_CUDA_TRY(cudaGetLastError());
-    h->prof.launches += 1;
-    int jdone = 0;
-    for (int j = 0; j < m && its < h->opt.maxit; ++j) {
-      double2* vj = k.V + (long long)j * nrhs * nf;
-      double2* w = k.V + (long long)(j + 1) * nrhs * nf;
-      // z = M^{-1} v_j ; w = A z
-      const VType vt = mixed ? VType::DF : VType::C128, zt = mixed ? VType::C64 : VType::C128;
-      if (pc) {
-        HPS_CUDA_TRY(ops.precond(vt, vj, zt, k.z, nrhs, st));
-        HPS_CUDA_TRY(ops.apply(zt, k.z, vt, w, nrhs, st));
-      } else if (vc32) {
-        HPS_CUDA_TRY(ops.apply(VType::C64, vc32, vt, w, nrhs, st));
-      } else {
-        HPS_CUDA_TRY(ops.apply(vt, vj, vt, w, nrhs, st));
+    HPS_CUDA_TRY(cudaMemcpyAsync(k.g, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    const int steps = std::min(m, h->opt.maxit - its);
+    const bool use_graph = !fl.no_graph && steps == m;
+    bool replayed = false;
+    if (use_graph) {
+      CycleGraph& gr = k.graph;
+      const bool match = gr.exec && gr.nrhs == nrhs && gr.m == m && gr.ops_id == ops.id && gr.mixed == (int)mixed &&
+                         gr.pc == (int)pc && gr.c64op == (vc32 != nullptr) && gr.cgs2 == (int)cgs2 &&
+                         gr.prof == (int)h->prof.on && gr.n == nf && gr.V == (const void*)k.V;
+      if (!match) {
+        destroy_graph(h);
+        // capture on the handle's own stream (the caller's may be the legacy default stream,
+        // which cannot be captured); the graph is launched on the caller's stream
+        cudaStream_t cs = h->stream;
+        HPS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        const long long l0 = h->prof.launches;
+        const size_t r0 = h->prof.recs.size();
+        h->gate = any_active;
+        int crc = first_vector(cs);
+        for (int j = 0; j < m && crc == HPS_OK; ++j) crc = step(j, cs);
+        h->gate = nullptr;
+        h->prof.step = -1;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        std::vector<Profiler::Rec> recs = h->prof.take_recs(r0);
+        const long long nl = h->prof.launches - l0;
+        h->prof.launches = l0;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ie = cudaSuccess;
+        if (crc == HPS_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (crc != HPS_OK || ce != cudaSuccess || ie != cudaSuccess) {
+          h->prof.release(recs);
+          cudaGetLastError();
+          if (crc != HPS_OK) return crc;
+          set_error(std::string("capture of the GMRES cycle failed: ") +
+                    cudaGetErrorString(ce != cudaSuccess ? ce : ie));
+          return HPS_ECUDA;
+        }
+        gr.exec = exec;
+        gr.nrhs = nrhs;
+        gr.m = m;
+        gr.ops_id = ops.id;
+        gr.mixed = mixed;
+        gr.pc = pc;
+        gr.c64op = vc32 != nullptr;
+        gr.cgs2 = cgs2;
+        gr.prof = h->prof.on;
+        gr.n = nf;
+        gr.V = k.V;
+        gr.launches = nl;
+        gr.recs = std::move(recs);
       }
-      VecArgs va;
-      va.V = k.V;
-      va.w = w;
-      va.nf = nf;
-      va.nrhs = nrhs;
-      va.nvec = j + 1;
-      va.M1 = M1;
-      va.nblk = k.nblk;
-      va.part = k.part;
-      va.active = active;
-      const dim3 bgrid(k.nblk, nrhs);
-      DfArgs da;
-      da.V = (const float4*)k.V;
-      da.w = (float4*)w;
-      da.nf = nf;
-      da.nrhs = nrhs;
-      da.nvec = j + 1;
-      da.M1 = M1;
-      da.nblk = k.nblk;
-      da.part = k.part;
-      da.active = active;
-      cudaEvent_t ev_arn = h->prof.begin(st);
-      if (mixed) mdot_df_kernel<<<bgrid, kT, 0, st>>>(da);
-      else mdot_kernel<<<bgrid, kT, 0, st>>>(va);
-      HPS_CUDA_TRY(cudaGetLastError());
-      reduce_kernel<<<dim3(j + 1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, k.hcol, M1 + 1, 0, active);
-      HPS_CUDA_TRY(cudaGetLastError());
-      va.coef = da.coef = k.hcol;
-      va.cstride = da.cstride = M1 + 1;
-      if (mixed) axpy_df_kernel<<<bgrid, kT, 0, st>>>(da, 1);
-      else axpy_kernel<<<bgrid, kT, 0, st>>>(va, 1);
-      HPS_CUDA_TRY(cudaGetLastError());
-      reduce_kernel<<<dim3(j + 1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, h2, M1, 0, active);
-      HPS_CUDA_TRY(cudaGetLastError());
-      va.coef = da.coef = h2;
-      va.cstride = da.cstride = M1;
-      if (mixed) axpy_df_kernel<<<bgrid, kT, 0, st>>>(da, 2);
-      else axpy_kernel<<<bgrid, kT, 0, st>>>(va, 2);
-      HPS_CUDA_TRY(cudaGetLastError());
-      reduce_kernel<<<dim3(1, nrhs), kT, 0, st>>>(k.part, k.nblk, M1, k.hcol + M1, M1 + 1, 0, active);
-      HPS_CUDA_TRY(cudaGetLastError());
-      HPS_CUDA_TRY(cudaMemsetAsync(any_active, 0, sizeof(int), st));
-      GivensArgs ga;
-      ga.nrhs = nrhs;
-      ga.m = m;
-      ga.j = j;
-      ga.M1 = M1;
-      ga.nblk = k.nblk;
-      ga.part = k.part;
-      ga.hcol = k.hcol;
-      ga.h2 = h2;
-      ga.H = k.H;
-      ga.cs = k.cs;
-      ga.sn = k.sn;
-      ga.g = k.g;
-      ga.est = est;
-      ga.invn = invn;
-      ga.active = active;
-      ga.kcount = kcount;
-      ga.target = target;
-      ga.any_active = any_active;
-      givens_kernel<<<nrhs, 64, 0, st>>>(ga);
-      HPS_CUDA_TRY(cudaGetLastError());
-      if (mixed) scale_df_kernel<<<vgrid, 256, 0, st>>>((float4*)w, nf, invn, vc32);
-      else scale_kernel<<<vgrid, 256, 0, st>>>(w, nf, nrhs, invn, nullptr);
-      HPS_CUDA_TRY(cudaGetLastError());
-      h->prof.end(HPS_PHASE_ARNOLDI, ev_arn, st);
-      h->prof.launches += 8;
-      ++its;
-      jdone = j + 1;
-      int hany = 0;
-      HPS_CUDA_TRY(cudaMemcpyAsync(&hany, any_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-      HPS_CUDA_TRY(cudaStreamSynchronize(st));
-      if (!hany) break;
+      HPS_CUDA_TRY(cudaGraphLaunch(gr.exec, st));
+      h->prof.launches += gr.launches;
+      replayed = true;
+    } else {
+      if ((rc = first_vector(st))) return rc;
+      for (int j = 0; j < steps; ++j) {
+        if ((rc = step(j, st))) return rc;
+        int hany = 0;
+        HPS_CUDA_TRY(cudaMemcpyAsync(&hany, any_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!hany) break;
+      }
     }
     // x += M^{-1} (V y)
     cudaEvent_t ev_up = h->prof.begin(st);
     lsq_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, m, M1, k.H, k.g, kcount, k.y);
     HPS_CUDA_TRY(cudaGetLastError());
-    if (mixed) combine_df_kernel<<<vgrid, 256, 0, st>>>((const float4*)k.V, nrhs, nf, jdone, m, k.y, k.u);
-    else combine_kernel<<<vgrid, 256, 0, st>>>(k.V, nrhs, nf, jdone, m, k.y, k.u);
+    if (mixed) combine_df_kernel<<<vgrid, 256, 0, st>>>((const float4*)k.V, nrhs, nf, kcount, m, k.y, k.u);
+    else combine_kernel<<<vgrid, 256, 0, st>>>(k.V, nrhs, nf, kcount, m, k.y, k.u);
     HPS_CUDA_TRY(cudaGetLastError());
     const long long nall = (long long)nrhs * nf;
     if (pc) {
@@ -883,9 +1029,15 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
     HPS_CUDA_TRY(cudaGetLastError());
     h->prof.end(HPS_PHASE_UPDATE, ev_up, st);
     h->prof.launches += 3;
-    // true residual r = b - A x in FP64
+    // true residual r = b - A x in FP64; its norms, the step counts and the
+    // reorthogonalization count are the cycle's read-back
     HPS_CUDA_TRY(ops.residual(x, b, k.r, nrhs, st));
-    if ((rc = vec_norms(h, k.r, nrhs, rnorm, st))) return rc;
+    if ((rc = vec_norms(h, k.r, nrhs, rnorm, st, k.active, hread.data(), 3 * nrhs + 3))) return rc;
+    int done = 0;
+    for (int r = 0; r < nrhs; ++r) done = std::max(done, hread[nrhs + r]);
+    nre_total += hread[3 * nrhs + 2];
+    if (replayed && h->prof.on) h->prof.read_recs(k.graph.recs, done);
+    its += done;
     if (h->tc_error) {
       int terr = 0;
       HPS_CUDA_TRY(cudaMemcpy(&terr, h->tc_error, sizeof(int), cudaMemcpyDeviceToHost));
@@ -895,6 +1047,7 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
       }
     }
     ++cycles;
+    if (done == 0) break;  // nothing was active: no progress possible
   }
   double rel = 0.0;
   for (int r = 0; r < nrhs; ++r)
@@ -905,6 +1058,7 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
     info->converged = converged ? 1 : 0;
     info->rel_residual = rel;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->reorth_steps = (int)std::min<long long>(nre_total, 0x7fffffff);
   }
   if (!converged) {
     set_error("GMRES did not reach the tolerance within maxit iterations");
@@ -917,7 +1071,7 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
 // apply.cu; FP64 residual with the FP64 maps (in lean mode the FP32 maps
 // against FP64 vectors).
 int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs, double tol, hps_solve_info* info,
-                cudaStream_t st, bool use_precond) {
+                cudaStream_t st, bool use_precond, SolveFlags fl) {
   const bool mixed = (form == HPS_FORM_MIXED);
   GmresOps ops;
   ops.n = h->nf;
@@ -932,7 +1086,8 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
     return timed_apply(h, HPS_PHASE_RESIDUAL, h->R64 == nullptr, VType::C128, xx, VType::C128, r, bb, nrhs, true, s);
   };
   ops.c64_operand = mixed && apply_tc_eligible(h, nrhs);
-  return gmres_core(h, ops, mixed, b, x, nrhs, tol, info, st);
+  ops.id = 0;
+  return gmres_core(h, ops, mixed, b, x, nrhs, tol, info, st, fl);
 }
 
 }  // namespace hps

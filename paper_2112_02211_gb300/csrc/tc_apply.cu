@@ -64,6 +64,7 @@ struct TcArgs {
   void* y;          // output [rhs][nf]: float2 or double-float float4
   int out_df;
   int* error;
+  const int* gate;  // while a GMRES cycle is replayed: 0 = no right-hand side active, return at once
 };
 
 struct __align__(8) Bars {
@@ -79,6 +80,7 @@ struct __align__(8) Bars {
 
 __global__ void __launch_bounds__(kThreads, 1)
     tc_apply_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapF, TcArgs a) {
+  if (a.gate && *a.gate == 0) return;  // before any barrier or TMEM allocation
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the stage ring (swizzle atoms)
   unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -368,6 +370,7 @@ cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool 
     a.out_df = out_df ? 1 : 0;
     a.y = out_df ? (void*)((float4*)y + (long long)r0 * h->nf) : (void*)((float2*)y + (long long)r0 * h->nf);
     a.error = d_error;
+    a.gate = h->gate;
     const long long items = (long long)h->nl * mtiles;
     const int grid = (int)std::min<long long>(items, h->nsm);
     tc_apply_kernel<<<grid, kThreads, smem, st>>>(mapA, mapF, a);

@@ -60,6 +60,7 @@ struct PkArgs {
   const int* slot_lf;        // leaf*6 + face of each global slot
   float2* z;
   int* error;
+  const int* gate;  // while a GMRES cycle is replayed: 0 = no right-hand side active, return at once
 };
 
 struct __align__(8) Bars {
@@ -75,6 +76,7 @@ struct __align__(8) Bars {
 
 __global__ void __launch_bounds__(kThreads, 1)
     tc_precond_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapT, PkArgs a) {
+  if (a.gate && *a.gate == 0) return;  // before any barrier or TMEM allocation
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Bars* bars = reinterpret_cast<Bars*>(ring + kStages * kStageBytes);
@@ -310,6 +312,7 @@ cudaError_t launch_precond_tc(const hps_handle* h, const float2* t, float2* z, i
     a.slot_lf = h->dct.slot_lf;
     a.z = z;
     a.error = d_error;
+    a.gate = h->gate;
     const long long items = (long long)a.mtiles * a.ntiles;
     const int grid = (int)std::min<long long>(items, h->nsm);
     tc_precond_kernel<<<grid, kThreads, smem, st>>>(mapA, mapT, a);
