@@ -78,7 +78,7 @@ extern "C" {
  * instead of replaying the captured restart cycle (same arithmetic, same result bit for bit) */
 #define HPS_SOLVE_NO_GRAPH 64
 /* classical Gram-Schmidt twice at every step, instead of the second pass only where the
- * DGKS test asks for it */
+ * first cancelled most of the vector */
 #define HPS_SOLVE_CGS2 128
 
 typedef struct hps_handle hps_handle;
@@ -253,8 +253,9 @@ int hps_rhs(hps_handle* h, const double* s, const double* t, int nrhs, double* b
  * kernels of the following steps return at once after convergence.  The host
  * reads back once per cycle (residual norms and step counts).  Orthogonalization:
  * one classical Gram-Schmidt pass, and a second one at the steps where the
- * pass removed more than half of the vector's energy (DGKS criterion,
- * ||w'|| < ||w||/sqrt(2)); HPS_SOLVE_CGS2 forces the second pass everywhere.
+ * pass cancelled most of the vector (Rutishauser's criterion, ||w'|| <
+ * ||w||/10, which bounds the loss of orthogonality per step by ~10 eps);
+ * HPS_SOLVE_CGS2 forces the second pass everywhere.
  */
 int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs,
                     double tol, double* f_out, hps_solve_info* info, void* stream);

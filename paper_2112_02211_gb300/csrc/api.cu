@@ -116,7 +116,7 @@ void free_handle(hps_handle* h) {
                   h->dct.int_mask, h->dct.b_off, h->dct.leaf_bcls, h->dct.bc_rep, h->dct.kc_off,
                   h->dct.kc_slot_begin, h->dct.kslot_class, h->dct.kc_members, h->dct.kitems[0], h->dct.kitems[1],
                   h->dct.kitems[2], h->dct.kitems[3], h->dct.cl_tpos, h->dct.lf_tpos, h->dct.brd, h->dct.bto,
-                  h->dct.bsc, h->fs.d_cls, h->fs.Sinv64, h->fs.Sinv32, h->fs.eig};
+                  h->dct.bsc, h->dct.pos_class, h->fs.d_cls, h->fs.Sinv64, h->fs.Sinv32, h->fs.eig};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -314,7 +314,9 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
       const bool fp16 = want32 && (o.precond_fp16 || o.lean);
       // lean mode keeps K_c only in FP16, except when the shared blocks are few enough that
       // their complex-FP32 copies (needed by the tensor-core stage K) take at most 4 GiB
-      const bool kc32 = !o.lean || (!ct.kc_tc.empty() && ke * sizeof(float2) <= ((size_t)4 << 30));
+      // (and when solves with 64 or more right-hand sides will run stage K on the tensor cores)
+      const bool kc32 = !o.lean || (!ct.kc_tc.empty() && ke * sizeof(float2) <= ((size_t)4 << 30)) ||
+                        (o.tc_apply && ct.uniform && o.max_rhs >= 64);
       if (want32) {
         if (kc32 && (r = dalloc(h, (void**)&h->Kc32, ke * sizeof(float2)))) return r;
         if ((r = dalloc(h, (void**)&h->B32, be * sizeof(float2)))) return r;
@@ -384,8 +386,11 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
              (size_t)h.nl * 6 * sizeof(long long);  // stage-B offsets, t positions
     if (want64) bytes += (size_t)(ct.kc_elems + ct.b_elems) * c16;
     if (want32) bytes += (size_t)((o.lean ? 0 : ct.kc_elems) + ct.b_elems) * c8;
-    if (want32 && o.lean)  // complex-FP32 copies of shared blocks (if any), capped
-      bytes += std::min<size_t>((size_t)ct.kc_elems * c8, (size_t)4 << 30);
+    if (want32 && o.lean)  // complex-FP32 copies of shared blocks (if any), capped; all of them for
+                           // the multi-RHS tensor-core stage K
+      bytes += (o.tc_apply && ct.uniform && o.max_rhs >= 64) ? (size_t)ct.kc_elems * c8
+                                                              : std::min<size_t>((size_t)ct.kc_elems * c8, (size_t)4 << 30);
+    bytes += (size_t)ct.ncl * sizeof(int);  // stage-K position -> block
     if (want32 && (o.precond_fp16 || o.lean))
       bytes += (size_t)(ct.kc_elems + ct.b_elems) * sizeof(__half2) + nslots * q2 * sizeof(float) +
                (size_t)h.nl * 6 * q2 * sizeof(float);

@@ -354,7 +354,9 @@ __global__ void __launch_bounds__(kThreads) seg_gemv_kernel(const typename P::Ar
 // block.  B is stored transposed (column c holds the nint q^2 rows), so a warp
 // reads 32 consecutive rows of one column: coalesced loads and no cross-lane
 // reductions.  The external-face values are staged in shared memory; t at the
-// neighbours' internal slots gets r - B r_ext, z_ext = r_ext.
+// neighbours' internal slots gets r - B r_ext, z_ext = r_ext.  Several
+// right-hand sides: NR of them per pass over the block, each B entry loaded
+// once per pass and used NR times (rhs r of vector v at v + r * stride).
 template <class TM, class TIN, class TOUT>
 struct PrecBArgs {
   const TM* B;
@@ -368,6 +370,8 @@ struct PrecBArgs {
   const TIN* r;
   TOUT* z;
   TOUT* t;
+  int nrhs;
+  long long vstride, tstride;  // per right-hand side: r and z, t
   const int* gate;  // as in seg_gemv_kernel
 };
 
@@ -376,37 +380,52 @@ template <> __device__ __forceinline__ float2 load_one<__half2>(const __half2* p
 template <> __device__ __forceinline__ float2 load_one<float2>(const float2* p) { return *p; }
 template <> __device__ __forceinline__ double2 load_one<double2>(const double2* p) { return *p; }
 
-template <class TM, class TIN, class TOUT>
+template <class TM, class TIN, class TOUT, int NR>
 __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TIN, TOUT> A) {
   if (A.gate && *A.gate == 0) return;
   using Acc = typename MT<TM>::Acc;
   extern __shared__ __align__(16) unsigned char smraw[];
-  Acc* xs = reinterpret_cast<Acc*>(smraw);  // 6 q^2
+  Acc* xs = reinterpret_cast<Acc*>(smraw);  // NR x 3 q^2 (external columns)
   const int q2 = A.q2;
   for (int leaf = blockIdx.x; leaf < A.nl; leaf += gridDim.x) {
     const int nint = __popc((unsigned)A.int_mask[leaf]);
     const int ncols = (6 - nint) * q2, nrows = nint * q2;
-    __syncthreads();
-    for (int c = threadIdx.x; c < ncols; c += kThreads) {
-      const int k = c / q2;
-      const long long o = A.brd[leaf * 6 + nint + k] + (c - k * q2);
-      const Acc v = cvt<Acc>(A.r[o]);
-      xs[c] = v;
-      A.z[o] = cvt<TOUT>(v);
-    }
-    __syncthreads();
-    if (nint == 0) continue;
     const TM* Bm = A.B + A.b_off[leaf];
     const int ldr = (int)rup4(nrows);
-    for (int row = threadIdx.x; row < nrows; row += kThreads) {
-      Acc acc = czero<Acc>();
+    for (int r0 = 0; r0 < A.nrhs; r0 += NR) {
+      const int nr = min(NR, A.nrhs - r0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nr * ncols; idx += kThreads) {
+        const int rr = idx / ncols, c = idx - rr * ncols;
+        const int k = c / q2;
+        const long long o = (long long)(r0 + rr) * A.vstride + A.brd[leaf * 6 + nint + k] + (c - k * q2);
+        const Acc v = cvt<Acc>(A.r[o]);
+        xs[rr * ncols + c] = v;
+        A.z[o] = cvt<TOUT>(v);
+      }
+      __syncthreads();
+      if (nint == 0) continue;
+      for (int row = threadIdx.x; row < nrows; row += kThreads) {
+        Acc acc[NR];
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) acc[rr] = czero<Acc>();
 #pragma unroll 4
-      for (int c = 0; c < ncols; ++c) cfma(acc, load_one<TM>(Bm + (long long)c * ldr + row), xs[c]);
-      const int k = row / q2, j = row - k * q2;
-      const int e = leaf * 6 + k;
-      const Acc g = rscale(acc, A.bscale, (long long)A.bsc[e] + j);
-      const Acc v = csub(cvt<Acc>(A.r[A.brd[e] + j]), g);
-      A.t[A.bto[e] + j] = cvt<TOUT>(v);
+        for (int c = 0; c < ncols; ++c) {
+          const Acc bv = load_one<TM>(Bm + (long long)c * ldr + row);
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr)
+            if (rr < nr) cfma(acc[rr], bv, xs[rr * ncols + c]);
+        }
+        const int k = row / q2, j = row - k * q2;
+        const int e = leaf * 6 + k;
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+          if (rr >= nr) break;
+          const Acc g = rscale(acc[rr], A.bscale, (long long)A.bsc[e] + j);
+          const Acc v = csub(cvt<Acc>(A.r[(long long)(r0 + rr) * A.vstride + A.brd[e] + j]), g);
+          A.t[(long long)(r0 + rr) * A.tstride + A.bto[e] + j] = cvt<TOUT>(v);
+        }
+      }
     }
   }
 }
@@ -500,26 +519,45 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.nl = h->nl;
     A.q2 = q2;
     A.gate = h->gate;
+    A.r = r;
+    A.z = z;
+    A.t = t;
+    A.nrhs = nrhs;
+    A.vstride = h->nf;
+    A.tstride = tstride;
     using Acc = typename MT<TM>::Acc;
-    const size_t smem = (size_t)h->nb * sizeof(Acc);
-    auto kern = prec_b_kernel<TM, TIN, TOUT>;
     cudaEvent_t ev = h->prof.begin(st);
-    cudaError_t e = allow_dynamic_smem((const void*)kern, smem);
-    int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-    const int grid = (int)std::min<long long>(h->nl, (long long)h->nsm * std::max(occ, 1));
-    for (int rhs = 0; rhs < nrhs && e == cudaSuccess; ++rhs) {
-      A.r = r + (long long)rhs * h->nf;
-      A.z = z + (long long)rhs * h->nf;
-      A.t = t + (long long)rhs * tstride;
+    auto launch_b = [&](auto kern, int nr) -> cudaError_t {
+      const size_t smem = (size_t)nr * h->ct.max_ext * q2 * sizeof(Acc) + 16;
+      cudaError_t e2 = allow_dynamic_smem((const void*)kern, smem);
+      int occ = 0;
+      if (e2 == cudaSuccess) e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+      if (e2 != cudaSuccess) return e2;
+      const int grid = (int)std::min<long long>(h->nl, (long long)h->nsm * std::max(occ, 1));
       kern<<<grid, kThreads, smem, st>>>(A);
       ++h->prof.launches;
-      e = cudaGetLastError();
-    }
+      return cudaGetLastError();
+    };
+    // shared memory for NR x (the most external columns of any leaf: 3 q^2 when every
+    // cluster is 2x2x2, up to 6 q^2 for a leaf alone in its cluster)
+    cudaError_t e;
+    if (nrhs == 1) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 1>, 1);
+    else if (nrhs == 2) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 2>, 2);
+    else if (nrhs <= 4) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 4>, 4);
+    else e = launch_b(prec_b_kernel<TM, TIN, TOUT, 8>, 8);
     h->prof.end(HPS_PHASE_PRECOND_B, ev, st);
     if (e != cudaSuccess) return e;
   }
   if (h->ct.nslots == 0) return cudaSuccess;
+  if constexpr (std::is_same<TOUT, float2>::value) {
+    // many right-hand sides: every block once per 64 of them, on the tensor cores
+    if (precond_tc_multi_eligible(h, nrhs)) {
+      cudaEvent_t ev = h->prof.begin(st);
+      const cudaError_t e = launch_precond_tc_multi(h, (const float2*)t, (float2*)z, nrhs, h->tc_error, st);
+      h->prof.end(HPS_PHASE_PRECOND_K, ev, st);
+      return e;
+    }
+  }
   {
     using P = PrecKP<TM, TOUT, TOUT>;
     typename P::Args A;

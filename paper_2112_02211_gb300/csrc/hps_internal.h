@@ -72,6 +72,7 @@ struct ClusterTables {
   std::vector<int> slot_cluster;     // [nslots]
   std::vector<int> lf_slot;          // [nleaves*6] slot of (leaf, face) or -1 if external
   std::vector<uint8_t> int_mask;     // [nleaves] bit f: face f is internal to the leaf's cluster
+  int max_ext = 6;                   // most external faces of any leaf (3 when every cluster is 2x2x2)
   std::vector<long long> b_off;      // [nleaves] element offset of the leaf's B block
   // distinct K blocks
   int nkc = 0;
@@ -108,6 +109,13 @@ struct ClusterTables {
   // neighbour slot (internal faces); bsc = FP16 row-scale base (bcls*6 + face)*q^2
   std::vector<int> brd, bto, bsc;
   long long kc_elems = 0, b_elems = 0;
+  // Every block has the same internal size nint (all clusters 2x2x2), blocks are
+  // stored back to back (kc_off[k] = k nint ld), nint is a multiple of 16 and the
+  // member at stage-K position m (kc_members[m]) starts at t offset m nint: the
+  // blocks form one 3D array and t one [position][nint] matrix per right-hand
+  // side, so the multi-RHS tensor-core stage K runs every block in one launch.
+  bool uniform = false;
+  std::vector<int> pos_class;        // [ncl] K block of the member at stage-K position m
 };
 
 struct DeviceClusterTables {
@@ -130,6 +138,7 @@ struct DeviceClusterTables {
   int* brd = nullptr;
   int* bto = nullptr;
   int* bsc = nullptr;
+  int* pos_class = nullptr;
 };
 
 // Per-phase CUDA-event timing and a launch counter (see hps_profile).  Events
@@ -388,6 +397,12 @@ cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool 
 // the tensor cores (tc_precond.cu): z_int = K_c t for every member cluster of
 // those blocks; one right-hand side; t in the class-ordered layout.
 cudaError_t launch_precond_tc(const hps_handle* h, const float2* t, float2* z, int* d_error, cudaStream_t st);
+// Stage K for nrhs (a multiple of 64) right-hand sides at once, every block on the tensor cores
+// in one launch (complex-FP32 blocks, one TF32 product): the GEMM of each K_c against the
+// columns (member cluster, right-hand side).  Needs ct.uniform.  t: [rhs][tsize], z: [rhs][nf].
+bool precond_tc_multi_eligible(const hps_handle* h, int nrhs);
+cudaError_t launch_precond_tc_multi(const hps_handle* h, const float2* t, float2* z, int nrhs, int* d_error,
+                                    cudaStream_t st);
 // Timed wrappers (phase intervals recorded when profiling is on).
 cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType tin, const void* f, VType tout,
                         void* y, const double2* bvec, int nrhs, bool residual, cudaStream_t st);

@@ -943,6 +943,8 @@ void build_cluster_tables(hps_handle* h, int width) {
         ct.cl_leaf_begin.push_back((int)ct.cl_leaves.size());
         ct.cl_slot_begin.push_back(ct.nslots);
       }
+  ct.max_ext = 0;
+  for (int leaf = 0; leaf < h->nl; ++leaf) ct.max_ext = std::max(ct.max_ext, 6 - __builtin_popcount(ct.int_mask[leaf]));
   assign_blocks(h, nullptr);
 }
 
@@ -1096,6 +1098,19 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
           ct.brd[e] = leaf * h->nb + f * q2;
         }
       }
+  }
+  // one 3D array of blocks and one [position][nint] matrix of t (multi-RHS stage K)
+  ct.pos_class.assign(ct.ncl, 0);
+  for (int m = 0; m < ct.ncl; ++m) ct.pos_class[m] = ct.cl_class[ct.kc_members[m]];
+  ct.uniform = ct.nkc > 0;
+  {
+    const long long nint0 = ct.nkc > 0 ? (long long)(ct.kc_slot_begin[1] - ct.kc_slot_begin[0]) * q2 : 0;
+    if (nint0 == 0 || nint0 % 16 != 0) ct.uniform = false;
+    for (int k = 0; k < ct.nkc && ct.uniform; ++k)
+      if ((long long)(ct.kc_slot_begin[k + 1] - ct.kc_slot_begin[k]) * q2 != nint0 || ct.kc_off[k] != k * nint0 * nint0)
+        ct.uniform = false;
+    for (int m = 0; m < ct.ncl && ct.uniform; ++m)
+      if (ct.cl_tpos[ct.kc_members[m]] != m * nint0) ct.uniform = false;
   }
   // blocks for the tensor-core path: many members, an even row length (16-byte
   // aligned member rows of complex floats)
@@ -1291,6 +1306,7 @@ int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st
   if ((rc = upload(h, h->dct.brd, ct.brd, st))) return rc;
   if ((rc = upload(h, h->dct.bto, ct.bto, st))) return rc;
   if ((rc = upload(h, h->dct.bsc, ct.bsc, st))) return rc;
+  if ((rc = upload(h, h->dct.pos_class, ct.pos_class, st))) return rc;
   for (int i = 0; i < 4; ++i)
     if ((rc = upload(h, h->dct.kitems[i], ct.kitems[i], st))) return rc;
   HPS_CUDA_TRY(cudaStreamSynchronize(st));

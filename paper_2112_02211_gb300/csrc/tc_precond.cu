@@ -14,6 +14,13 @@
 // term (both operands rounded to TF32, 2^-11 relative, the precision of the
 // FP16 blocks used for the other clusters); FP32 accumulation in TMEM.
 //
+// Many right-hand sides (MULTI): every block against the columns (member
+// cluster, right-hand side) in one launch.  Items are (stage-K position m,
+// 128-row tile, 64-RHS tile); the blocks are one 3D array [block][row][col]
+// and t one [rhs][position][nint] array, so both tiles come from one tensor
+// map each: K_c rows of block pos_class[m], and the member's t for 64
+// right-hand sides (box 32 floats x 1 member x 64 rhs).
+//
 // Kernel (one CTA per SM, persistent over items = (128-row tile, 64-member tile)):
 //   warp 0       TMA producer: A tile (128 rows x 32 floats) and T tile
 //                (64 members x 32 floats), 128-byte swizzle, 5-stage ring
@@ -55,12 +62,16 @@ constexpr int kTmemCols = 256;
 
 struct PkArgs {
   int nint, nmem, mtiles, ntiles, kblocks, q2, nb;
-  const int* members;        // the block's member clusters (nmem)
+  const int* members;        // the block's member clusters (nmem); MULTI: all clusters in stage-K order
   const int* cl_slot_begin;  // first global slot of each cluster
   const int* slot_lf;        // leaf*6 + face of each global slot
   float2* z;
   int* error;
   const int* gate;  // while a GMRES cycle is replayed: 0 = no right-hand side active, return at once
+  // MULTI only
+  const int* pos_class;      // K block of the member at each stage-K position
+  int npos, rtiles, nrhs;
+  long long nf;              // right-hand-side stride of z
 };
 
 struct __align__(8) Bars {
@@ -74,6 +85,7 @@ struct __align__(8) Bars {
   int abort;
 };
 
+template <bool MULTI>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_precond_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapT, PkArgs a) {
   if (a.gate && *a.gate == 0) return;  // before any barrier or TMEM allocation
@@ -81,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Bars* bars = reinterpret_cast<Bars*>(ring + kStages * kStageBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long nitems = (long long)a.mtiles * a.ntiles;
+  const long long nitems = MULTI ? (long long)a.npos * a.mtiles * a.rtiles : (long long)a.mtiles * a.ntiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -118,7 +130,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       long long it = 0;
       bool ok = true;
       for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-        const int mt = (int)(item % a.mtiles), nt = (int)(item / a.mtiles);
+        int mt, nt, pos = 0, rt = 0, blk = 0;
+        if (MULTI) {
+          // item = (position, row tile, rhs tile), rhs tile fastest
+          pos = (int)(item / ((long long)a.mtiles * a.rtiles));
+          const int rem = (int)(item % ((long long)a.mtiles * a.rtiles));
+          mt = rem / a.rtiles;
+          rt = rem % a.rtiles;
+          nt = 0;
+          blk = a.pos_class[pos];
+        } else {
+          mt = (int)(item % a.mtiles);
+          nt = (int)(item / a.mtiles);
+        }
         for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t ph = (uint32_t)((it / kStages) & 1);
@@ -129,8 +153,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           unsigned char* st = ring + s * kStageBytes;
           mbar_expect_tx(&bars->full[s], kABytes + kTBytes);
-          tma_load_2d(st, &mapA, &bars->full[s], kb * kTileK, mt * kTileM);
-          tma_load_2d(st + kABytes + kBBytes, &mapT, &bars->full[s], kb * kTileK, nt * kMem);
+          if (MULTI) {
+            tma_load_3d(st, &mapA, &bars->full[s], kb * kTileK, mt * kTileM, blk);
+            tma_load_3d(st + kABytes + kBBytes, &mapT, &bars->full[s], kb * kTileK, pos, rt * kMem);
+          } else {
+            tma_load_2d(st, &mapA, &bars->full[s], kb * kTileK, mt * kTileM);
+            tma_load_2d(st + kABytes + kBBytes, &mapT, &bars->full[s], kb * kTileK, nt * kMem);
+          }
         }
       }
       for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j)
@@ -220,7 +249,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int mt = (int)(item % a.mtiles), nt = (int)(item / a.mtiles);
+      int mt, nt, pos = 0, rt = 0;
+      if (MULTI) {
+        pos = (int)(item / ((long long)a.mtiles * a.rtiles));
+        const int rem = (int)(item % ((long long)a.mtiles * a.rtiles));
+        mt = rem / a.rtiles;
+        rt = rem % a.rtiles;
+        nt = 0;
+      } else {
+        mt = (int)(item % a.mtiles);
+        nt = (int)(item / a.mtiles);
+      }
       const int row = mt * kTileM + ew * 32 + lane;
       const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(b * kTileN);
       float re[32], im[32];
@@ -230,13 +269,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld32(taddr + kMem + half * 32, im);
         if (row < a.nint) {
           const int sl = row / a.q2, j = row % a.q2;
+          if (MULTI) {
+            // columns: 64 right-hand sides of one member
+            const int cl = a.members[pos];
+            const int lf = a.slot_lf[a.cl_slot_begin[cl] + sl];
+            const long long o = (long long)(lf / 6) * a.nb + (long long)(lf % 6) * a.q2 + j;
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            const int m = nt * kMem + half * 32 + c;
-            if (m < a.nmem) {
-              const int cl = a.members[m];
-              const int lf = a.slot_lf[a.cl_slot_begin[cl] + sl];
-              a.z[(long long)(lf / 6) * a.nb + (long long)(lf % 6) * a.q2 + j] = make_float2(re[c], im[c]);
+            for (int c = 0; c < 32; ++c) {
+              const int rhs = rt * kMem + half * 32 + c;
+              if (rhs < a.nrhs) a.z[(long long)rhs * a.nf + o] = make_float2(re[c], im[c]);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              const int m = nt * kMem + half * 32 + c;
+              if (m < a.nmem) {
+                const int cl = a.members[m];
+                const int lf = a.slot_lf[a.cl_slot_begin[cl] + sl];
+                a.z[(long long)(lf / 6) * a.nb + (long long)(lf % 6) * a.q2 + j] = make_float2(re[c], im[c]);
+              }
             }
           }
         }
@@ -265,7 +316,7 @@ cudaError_t launch_precond_tc(const hps_handle* h, const float2* t, float2* z, i
   if (!encode) return cudaErrorNotSupported;
   const int q2 = h->q * h->q;
   const int smem = kStages * kStageBytes + (int)sizeof(Bars) + 1024;
-  cudaError_t e = allow_dynamic_smem((const void*)tc_precond_kernel, smem);
+  cudaError_t e = allow_dynamic_smem((const void*)tc_precond_kernel<false>, smem);
   if (e != cudaSuccess) return e;
   for (int k : ct.kc_tc) {
     const int ns = ct.kc_slot_begin[k + 1] - ct.kc_slot_begin[k];
@@ -313,14 +364,89 @@ cudaError_t launch_precond_tc(const hps_handle* h, const float2* t, float2* z, i
     a.z = z;
     a.error = d_error;
     a.gate = h->gate;
+    a.pos_class = nullptr;
+    a.npos = a.rtiles = a.nrhs = 0;
+    a.nf = 0;
     const long long items = (long long)a.mtiles * a.ntiles;
     const int grid = (int)std::min<long long>(items, h->nsm);
-    tc_precond_kernel<<<grid, kThreads, smem, st>>>(mapA, mapT, a);
+    tc_precond_kernel<false><<<grid, kThreads, smem, st>>>(mapA, mapT, a);
     ++h->prof.launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+bool precond_tc_multi_eligible(const hps_handle* h, int nrhs) {
+  return h->has_precond && h->opt.tc_apply && h->Kc32 && h->tc_error && h->ct.uniform && h->ct.nslots > 0 &&
+         nrhs >= kMem && nrhs % kMem == 0;
+}
+
+// z_int = K_c t for every cluster and nrhs right-hand sides: one launch, every
+// block on the tensor cores (see MULTI above).
+cudaError_t launch_precond_tc_multi(const hps_handle* h, const float2* t, float2* z, int nrhs, int* d_error,
+                                    cudaStream_t st) {
+  const ClusterTables& ct = h->ct;
+  if (!precond_tc_multi_eligible(h, nrhs) || !d_error) return cudaErrorInvalidValue;
+  auto encode = encoder();
+  if (!encode) return cudaErrorNotSupported;
+  const int q2 = h->q * h->q;
+  const int nint = (ct.kc_slot_begin[1] - ct.kc_slot_begin[0]) * q2;  // uniform: every block the same
+  const long long tstride = ct.tsize;
+  // TMA: 16-byte aligned bases and strides (checked, not assumed)
+  if ((reinterpret_cast<uintptr_t>(h->Kc32) | reinterpret_cast<uintptr_t>(t)) % 16 != 0 || (8LL * nint) % 16 != 0 ||
+      (8LL * tstride) % 16 != 0)
+    return cudaErrorInvalidValue;
+  const int smem = kStages * kStageBytes + (int)sizeof(Bars) + 1024;
+  cudaError_t e = allow_dynamic_smem((const void*)tc_precond_kernel<true>, smem);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mapA, mapT;
+  {
+    // [block][row][2 nint floats], rows nint apart (ld = nint: nint is a multiple of 16)
+    cuuint64_t dims[3] = {(cuuint64_t)(2 * nint), (cuuint64_t)nint, (cuuint64_t)ct.nkc};
+    cuuint64_t strides[2] = {(cuuint64_t)nint * 8, (cuuint64_t)nint * nint * 8};
+    cuuint32_t box[3] = {kTileK, kTileM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (encode(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)h->Kc32, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    // [rhs][position][2 nint floats]; box: 32 floats x 1 member x 64 right-hand sides
+    cuuint64_t dims[3] = {(cuuint64_t)(2 * nint), (cuuint64_t)ct.ncl, (cuuint64_t)nrhs};
+    cuuint64_t strides[2] = {(cuuint64_t)nint * 8, (cuuint64_t)tstride * 8};
+    cuuint32_t box[3] = {kTileK, 1, kMem};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (encode(&mapT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)t, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  PkArgs a;
+  a.nint = nint;
+  a.nmem = 0;
+  a.mtiles = (nint + kTileM - 1) / kTileM;
+  a.ntiles = 0;
+  a.kblocks = (2 * nint + kTileK - 1) / kTileK;
+  a.q2 = q2;
+  a.nb = h->nb;
+  a.members = h->dct.kc_members;
+  a.cl_slot_begin = h->dct.cl_slot_begin;
+  a.slot_lf = h->dct.slot_lf;
+  a.z = z;
+  a.error = d_error;
+  a.gate = h->gate;
+  a.pos_class = h->dct.pos_class;
+  a.npos = ct.ncl;
+  a.rtiles = nrhs / kMem;
+  a.nrhs = nrhs;
+  a.nf = h->nf;
+  const long long items = (long long)a.npos * a.mtiles * a.rtiles;
+  const int grid = (int)std::min<long long>(items, h->nsm);
+  tc_precond_kernel<true><<<grid, kThreads, smem, st>>>(mapA, mapT, a);
+  ++h->prof.launches;
+  return cudaGetLastError();
 }
 
 }  // namespace hps

@@ -5,9 +5,10 @@ and resuming from a stored iterate (initial guess).
 * Graph vs step-by-step: the same kernels on the same data in the same order; the graph only
   lets the steps after convergence return at once instead of stopping on the host.  Results
   must agree bit for bit, iteration counts exactly.
-* One Gram-Schmidt pass plus the DGKS test vs two passes: both orthogonalize to working
-  precision, so both reach the oracle's solution within the solve tolerance's bar, with
-  iteration counts within a few of each other.
+* One Gram-Schmidt pass plus a second where the first cancelled most of the vector
+  (Rutishauser's test, ||w'|| < ||w||/10) vs two passes at every step: both keep the basis
+  orthogonal to ~10 eps, so both reach the oracle's solution within the solve tolerance's bar,
+  with iteration counts within a few of each other.
 * Resume: a solve started from its own converged answer does no iteration; one stopped early
   (maxit) and resumed reaches the same solution as an uninterrupted solve.
 """
