@@ -168,17 +168,26 @@ struct Profiler {
     pool.pop_back();
     return e;
   }
+  // An event record on st: an external event node of the graph while st is being
+  // captured (the flag is only valid then), a plain record otherwise.
+  static void record(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, st);
+  }
   // Start of a timed interval on stream st (nullptr when timing is off).
   cudaEvent_t begin(cudaStream_t st) {
     if (!on) return nullptr;
     cudaEvent_t e = take();
-    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    record(e, st);
     return e;
   }
   void end(int phase, cudaEvent_t a, cudaStream_t st) {
     if (!on || !a) return;
     cudaEvent_t e = take();
-    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    record(e, st);
     recs.push_back({phase, a, e, step});
   }
   // Intervals recorded since `from` (into a graph being captured); their events now
