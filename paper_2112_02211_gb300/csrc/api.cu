@@ -110,7 +110,7 @@ void free_handle(hps_handle* h) {
   cudaSetDevice(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
   krylov_free(h);
-  void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->H32, h->lambda, h->lambda_q, h->Kc64, h->Kc32, h->B64,
+  void* ptrs[] = {h->tables, h->R64, h->R32, h->H64, h->H32, h->R16lo, h->R16ls, h->H16lo, h->H16ls, h->lambda, h->lambda_q, h->Kc64, h->Kc32, h->B64,
                   h->B32, h->pc_scratch, h->Kc16, h->Kc16s, h->B16, h->B16s, h->tc_error, h->cdiag,
                   h->dct.slot_lf, h->dct.slot_cluster, h->dct.cl_slot_begin, h->dct.cl_kc_off, h->dct.lf_slot,
                   h->dct.int_mask, h->dct.b_off, h->dct.leaf_bcls, h->dct.bc_rep, h->dct.kc_off,
@@ -282,6 +282,12 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
     if (want32 && (r = dalloc(h, (void**)&h->R32, rel * sizeof(float2)))) return r;
     if (!o.lean && (r = dalloc(h, (void**)&h->H64, hel * sizeof(double2)))) return r;
     if (o.lean && (r = dalloc(h, (void**)&h->H32, hel * sizeof(float2)))) return r;
+    if (o.lean) {
+      if ((r = dalloc(h, (void**)&h->R16lo, rel * sizeof(__half2)))) return r;
+      if ((r = dalloc(h, (void**)&h->R16ls, (size_t)h->nl * h->nb * sizeof(float)))) return r;
+      if ((r = dalloc(h, (void**)&h->H16lo, hel * sizeof(__half2)))) return r;
+      if ((r = dalloc(h, (void**)&h->H16ls, (size_t)h->nl * h->nb * sizeof(float)))) return r;
+    }
     if ((r = dalloc(h, (void**)&h->lambda, (size_t)h->nl * sizeof(double2)))) return r;
     if ((r = dalloc(h, (void**)&h->tc_error, sizeof(int)))) return r;
     HPS_CUDA_TRY(cudaMemsetAsync(h->tc_error, 0, sizeof(int), st));
@@ -370,6 +376,8 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
   const size_t hel = (size_t)h.nl * h.nb * h.ldH;
   size_t bytes = h.tl.total * sizeof(double) + (o.lean ? 0 : rel * c16) + (want32 ? rel * c8 : 0) +
                  hel * (o.lean ? c8 : c16) + (size_t)h.nl * c16;
+  if (o.lean)  // FP16 remainders of R and H and their row scales
+    bytes += (rel + hel) * sizeof(__half2) + (size_t)2 * h.nl * h.nb * sizeof(float);
   const int q2 = h.q * h.q;
   size_t nslots = 0, tsize = 1;
   if (o.cluster == 2) {
@@ -423,11 +431,12 @@ int hps_apply(hps_handle* h, int dtype, const void* f, void* y, int nrhs, void* 
   HPS_CUDA_TRY(cudaSetDevice(h->dev));
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == HPS_C128) {
-    if (!h->R64) {
-      set_error("hps_apply: complex-double maps are not kept in lean mode");
+    if (!h->R64 && !h->R16lo) {
+      set_error("hps_apply: complex-double applies need the FP64 or the compensated FP32 maps");
       return HPS_EINVAL;
     }
-    HPS_CUDA_TRY(launch_apply(h, false, VType::C128, f, VType::C128, y, nullptr, nrhs, false, st));
+    // lean mode: the compensated FP32 maps (FP64-accurate, double-float accumulation)
+    HPS_CUDA_TRY(launch_apply(h, h->R64 == nullptr, VType::C128, f, VType::C128, y, nullptr, nrhs, false, st));
   } else if (dtype == HPS_C64) {
     if (!h->R32) {
       set_error("hps_apply: complex-FP32 operators were not built (HPS_FORM_MIXED)");

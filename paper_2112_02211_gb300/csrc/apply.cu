@@ -619,6 +619,9 @@ cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const
   }
   // the residual form b - (I + Pi R) f only exists for complex-double vectors
   if (bvec && !(tin == VType::C128 && tout == VType::C128)) return cudaErrorInvalidValue;
+  // complex-double vectors on a lean handle: the compensated FP32 maps (FP64-accurate)
+  if (tin == VType::C128 && tout == VType::C128 && compensated_maps(h)) return launch_apply_cf(h, (const double2*)f,
+                                                                                               (double2*)y, bvec, nrhs, st);
   const bool tc = apply_tc_eligible(h, nrhs) && !bvec;
   if (tc && tin == VType::C64 && tout == VType::C64)
     return launch_apply_tc(h, (const float2*)f, y, false, nrhs, h->tc_error, st);
@@ -673,6 +676,7 @@ cudaError_t rhs_t(const hps_handle* h, const TM* H, const double2* s, const doub
 cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
                        cudaStream_t st) {
   if (h->H64) return rhs_t(h, h->H64, s, t, b, nrhs, st);
+  if (h->H16lo) return launch_rhs_cf(h, s, t, b, nrhs, st);
   return rhs_t(h, h->H32, s, t, b, nrhs, st);
 }
 

@@ -317,6 +317,12 @@ struct hps_handle {
   float2* R32 = nullptr;   // nl x nb x ldR
   double2* H64 = nullptr;  // nl x nb x ldH
   float2* H32 = nullptr;   // nl x nb x ldH (lean mode instead of H64)
+  // lean mode: remainders M - M32 of the FP32 maps in FP16, row r of leaf l scaled by
+  // *16ls[l * nb + r] (compensated FP32 maps, compensated.cu)
+  __half2* R16lo = nullptr;
+  float* R16ls = nullptr;
+  __half2* H16lo = nullptr;
+  float* H16ls = nullptr;
   double2* lambda = nullptr;    // nl: homogenized constants lambda^tau
   double2* lambda_q = nullptr;  // nl: lambda^tau after binning (opt.lambda_bin), used by the preconditioner
   double2* cdiag = nullptr;   // nl x ni: C = kappa^2 (1 - b) at interior nodes (kept for recovery)
@@ -415,6 +421,14 @@ cudaError_t launch_precond_tc_multi(const hps_handle* h, const float2* t, float2
 // Timed wrappers (phase intervals recorded when profiling is on).
 cudaError_t timed_apply(const hps_handle* h, int phase, bool fp32_matrix, VType tin, const void* f, VType tout,
                         void* y, const double2* bvec, int nrhs, bool residual, cudaStream_t st);
+
+// ---- compensated.cu (lean mode: FP32 maps + FP16 remainders, double-float accumulation) ----
+cudaError_t launch_split_lo(const double2* M, long long rows, int ld, __half2* lo, float* scale, cudaStream_t st);
+bool compensated_maps(const hps_handle* h);
+cudaError_t launch_apply_cf(const hps_handle* h, const double2* x, double2* y, const double2* b, int nrhs,
+                            cudaStream_t st);
+cudaError_t launch_rhs_cf(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
+                          cudaStream_t st);
 
 // ---- full.cu (the paper's global-system path) ----
 cudaError_t launch_full_apply(const hps_handle* h, bool fp64, VType tin, const void* u, VType tout, void* y,

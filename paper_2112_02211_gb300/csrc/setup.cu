@@ -894,6 +894,13 @@ int build_exact_maps(hps_handle* h, const double2* cdiag, cudaStream_t st) {
         cast_kernel<<<1024, 256, 0, st>>>(Hb, h->H32 + (long long)l0 * nb * h->ldH, cnt);
         HPS_CUDA_TRY(cudaGetLastError());
       }
+      // lean mode: the FP16 remainders that make the FP32 maps FP64-accurate
+      if (h->R16lo)
+        HPS_CUDA_TRY(launch_split_lo(Rb, (long long)nbt * nb, h->ldR, h->R16lo + (long long)l0 * nb * h->ldR,
+                                     h->R16ls + (long long)l0 * nb, st));
+      if (h->H16lo)
+        HPS_CUDA_TRY(launch_split_lo(Hb, (long long)nbt * nb, h->ldH, h->H16lo + (long long)l0 * nb * h->ldH,
+                                     h->H16ls + (long long)l0 * nb, st));
       return HPS_OK;
     };
     rc = body();

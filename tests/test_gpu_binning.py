@@ -181,15 +181,15 @@ def test_lean_mode_keeps_shared_blocks_on_tensor_cores(tc_case):
         assert rel(z, ref) < 5e-3
         z16 = solver.precond(torch.from_numpy(r).cuda(), fp16_blocks=True).cpu().numpy()
         assert rel(z16, ref) < 5e-3
-        # lean mode forms the restart residual with FP32 maps and FP32 accumulation: its floor is
-        # ~3e-7 relative on this case, so it is run at the tolerances it is meant for (>= 1e-5)
-        f, info = solver.solve(t=torch.from_numpy(t.reshape(-1)).cuda(), tol=1e-5, form="mixed")
+        # the restart residual uses the FP32 maps plus their FP16 remainders with double-float
+        # accumulation (FP64-accurate), so lean solves meet the mixed form's bar
+        f, info = solver.solve(t=torch.from_numpy(t.reshape(-1)).cuda(), tol=1e-8, form="mixed")
         assert info["converged"], info
         xi, xf = O.interior_nodes(grid), O.face_nodes(grid)
         nrm = np.broadcast_to(O.face_normals()[None, :, None, :], xf.shape)
         prob = O.build_problem(grid, w.kappa, w.eta, w.sample_b(xi))
         rhs = O.rhs_face(grid, prob.H, None, w.sample_t(xf, nrm)[0])
         f_ref, _, _ = O.gmres(lambda v: O.apply_face(grid, prob.R, v), rhs, tol=1e-12, restart=50)
-        assert rel(f.cpu().numpy(), f_ref) < 1e-3
+        assert rel(f.cpu().numpy(), f_ref) < 1e-6
     finally:
         solver.close()
