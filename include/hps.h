@@ -365,6 +365,23 @@ long long hps_export(hps_handle* h, int what, int index, double* host_out);
  * non-finite entry. */
 int hps_import_map(hps_handle* h, int what, int index, const double* host_in);
 
+/*
+ * Test hook for the bounded device waits (no counterpart in the paper).  Every
+ * wait of the tensor-core kernels on an mbarrier is bounded: after a limit the
+ * CTA sets the handle's error word, stops issuing work, waits (bounded) for its
+ * own copies and tensor-core operations, frees its tensor memory and returns,
+ * and the solve returns HPS_ETIMEOUT with the GPU context intact.  With
+ * what = HPS_INJECT_SKIP_ARRIVAL, one warp of CTA 0 of the multi-RHS
+ * tensor-core apply leaves out one arrival, so that the MMA-issuing thread's
+ * wait runs out; spin_limit (> 0) replaces the wait limit (tries of
+ * mbarrier.try_wait) of that kernel, 0 keeps the default.  HPS_INJECT_NONE
+ * with spin_limit 0 restores normal operation.  Drops the handle's captured
+ * GMRES cycle.  For tests of the time-out path only.
+ */
+#define HPS_INJECT_NONE 0
+#define HPS_INJECT_SKIP_ARRIVAL 1
+int hps_test_inject(hps_handle* h, int what, long long spin_limit);
+
 /* Phases timed by the profiler (indices into hps_profile.ms / count). */
 #define HPS_PHASE_APPLY 0     /* w = A z inside the Arnoldi loop (working precision) */
 #define HPS_PHASE_PRECOND_B 1 /* preconditioner stage B: z_ext = r_ext, t = r_int - B r_ext */

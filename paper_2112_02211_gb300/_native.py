@@ -22,6 +22,8 @@ HPS_SOLVE_NO_PRECOND = 16
 HPS_SOLVE_X0 = 32
 HPS_SOLVE_NO_GRAPH = 64
 HPS_SOLVE_CGS2 = 128
+HPS_INJECT_NONE = 0
+HPS_INJECT_SKIP_ARRIVAL = 1
 HPS_PRECOND_NOALLOC_MAX_BYTES = 16 << 20
 HPS_EXPORT_R = 0
 HPS_EXPORT_H = 1
@@ -73,6 +75,7 @@ SIGNATURES = {
     "hps_recover": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "hps_export": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "hps_import_map": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "hps_test_inject": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
     "hps_full_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_full_precond": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_full_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P,

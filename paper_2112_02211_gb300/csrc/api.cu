@@ -846,6 +846,17 @@ int hps_import_map(hps_handle* h, int what, int index, const double* host_in) {
   return HPS_OK;
 }
 
+int hps_test_inject(hps_handle* h, int what, long long spin_limit) {
+  if (!h || (what != HPS_INJECT_NONE && what != HPS_INJECT_SKIP_ARRIVAL) || spin_limit < 0) {
+    set_error("hps_test_inject: bad arguments");
+    return HPS_EINVAL;
+  }
+  h->test_skip_arrival = (what == HPS_INJECT_SKIP_ARRIVAL) ? 1 : 0;
+  h->test_spin = spin_limit;
+  krylov_drop_graph(h);  // a captured cycle would keep the old launch parameters
+  return HPS_OK;
+}
+
 int hps_profile_enable(hps_handle* h, int on) {
   if (!h) {
     set_error("hps_profile_enable: NULL handle");

@@ -349,6 +349,10 @@ struct hps_handle {
   // (apply, preconditioner) read first, returning at once when it is 0 (no
   // right-hand side still active).  nullptr otherwise.
   mutable const int* gate = nullptr;
+  // test hook of hps_test_inject: bounded-wait limit (tries) of the tensor-core apply (0 =
+  // default) and whether one of its CTAs skips one mbarrier arrival
+  long long test_spin = 0;
+  int test_skip_arrival = 0;
   hps::KrylovSpace ks;
   mutable hps::Profiler prof;
   size_t bytes = 0;
@@ -439,6 +443,8 @@ cudaError_t launch_full_precond(const hps_handle* h, bool fp64, VType tin, const
 // ---- krylov.cu ----
 int krylov_alloc(hps_handle* h, int nrhs, long long nvec = -1);
 void krylov_free(hps_handle* h);
+// Drops the captured GMRES cycle (its launches carry parameters that changed).
+void krylov_drop_graph(hps_handle* h);
 // Operators of one restarted GMRES: w = A z (inner precision), z = M^{-1} v,
 // and the FP64 residual r = b - A x, on vectors of length n per right-hand side.
 struct GmresOps {

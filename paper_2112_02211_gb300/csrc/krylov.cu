@@ -716,6 +716,8 @@ void destroy_graph(hps_handle* h) {
 }
 }  // namespace
 
+void krylov_drop_graph(hps_handle* h) { destroy_graph(h); }
+
 void krylov_free(hps_handle* h) {
   destroy_graph(h);
   h->prof.destroy();
@@ -903,6 +905,8 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
     return HPS_OK;
   };
 
+  // the tensor-core kernels' error word starts clear for every solve
+  if (h->tc_error) HPS_CUDA_TRY(cudaMemsetAsync(h->tc_error, 0, sizeof(int), st));
   std::vector<double> bnorm, rnorm;
   if ((rc = vec_norms(h, b, nrhs, bnorm, st))) return rc;
   if (fl.x0) {

@@ -65,6 +65,8 @@ struct TcArgs {
   int out_df;
   int* error;
   const int* gate;  // while a GMRES cycle is replayed: 0 = no right-hand side active, return at once
+  long long spin;   // tries per bounded wait
+  int skip_arrival; // test hook: CTA 0's first transform warp does not arrive on the first stage
 };
 
 struct __align__(8) Bars {
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t ph = (uint32_t)((it / kStages) & 1);
-          if (bars->abort || (it >= kStages && !mbar_wait(&bars->empty[s], ph ^ 1))) {
+          if (bars->abort || (it >= kStages && !mbar_wait(&bars->empty[s], ph ^ 1, a.spin))) {
             fail();
             ok = false;
             break;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // copies still in flight land before the CTA leaves (bounded wait)
       for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j)
-        if (!mbar_wait(&bars->full[(int)(j % kStages)], (uint32_t)((j / kStages) & 1))) fail();
+        if (!mbar_wait(&bars->full[(int)(j % kStages)], (uint32_t)((j / kStages) & 1), a.spin)) fail();
     }
   } else if (warp >= 2 && warp < 8) {
     // ---------------- split into TF32 hi/lo operands ----------------
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
         const int s = (int)(it % kStages);
         const uint32_t ph = (uint32_t)((it / kStages) & 1);
-        if (bars->abort || !mbar_wait(&bars->full[s], ph)) {
+        if (bars->abort || !mbar_wait(&bars->full[s], ph, a.spin)) {
           fail();
           goto split_done;
         }
@@ -184,7 +186,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // make the generic-proxy writes visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bars->split[s]);
+        // (test hook: one missing arrival makes the MMA issuer's bounded wait run out)
+        const bool skip = a.skip_arrival && blockIdx.x == 0 && warp == 2 && it == 0;
+        if (lane == 0 && !skip) mbar_arrive(&bars->split[s]);
       }
     }
   split_done:;
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++local) {
         const int b = (int)(local & 1);
         const uint32_t acc = tmem + (uint32_t)(b * kTileN);
-        if (local >= 2 && !mbar_wait(&bars->acc_empty[b], (uint32_t)(((local >> 1) - 1) & 1))) {
+        if (local >= 2 && !mbar_wait(&bars->acc_empty[b], (uint32_t)(((local >> 1) - 1) & 1), a.spin)) {
           fail();
           ok = false;
           break;
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t ph = (uint32_t)((it / kStages) & 1);
-          if (bars->abort || !mbar_wait(&bars->split[s], ph)) {
+          if (bars->abort || !mbar_wait(&bars->split[s], ph, a.spin)) {
             fail();
             ok = false;
             break;
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // every MMA issued above completes before TMEM is freed (bounded wait)
       mma_commit(&bars->drain);
-      if (!mbar_wait(&bars->drain, 0)) fail();
+      if (!mbar_wait(&bars->drain, 0, a.spin)) fail();
     }
     __syncwarp();
   } else {
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     long long local = 0;
     for (long long item = blockIdx.x; item < nitems; item += gridDim.x, ++local) {
       const int b = (int)(local & 1);
-      if (bars->abort || !mbar_wait(&bars->acc_full[b], (uint32_t)((local >> 1) & 1))) {
+      if (bars->abort || !mbar_wait(&bars->acc_full[b], (uint32_t)((local >> 1) & 1), a.spin)) {
         fail();
         break;
       }
@@ -371,6 +375,8 @@ cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool 
     a.y = out_df ? (void*)((float4*)y + (long long)r0 * h->nf) : (void*)((float2*)y + (long long)r0 * h->nf);
     a.error = d_error;
     a.gate = h->gate;
+    a.spin = h->test_spin > 0 ? h->test_spin : kSpinLimit;
+    a.skip_arrival = h->test_skip_arrival;
     const long long items = (long long)h->nl * mtiles;
     const int grid = (int)std::min<long long>(items, h->nsm);
     tc_apply_kernel<<<grid, kThreads, smem, st>>>(mapA, mapF, a);
