@@ -121,6 +121,10 @@ typedef struct {
                          (leaves: one B block).  0 (default) keeps every lambda^tau; blocks are
                          still shared where values are bitwise equal.  Finite, >= 0.  Changes the
                          preconditioner only, never the converged solution. */
+  int autotune;       /* time the candidate launch shapes (rows per warp, resident CTAs per SM)
+                         of the ItI apply and of the preconditioner's stage K at setup and keep
+                         the fastest (hps_launch_shapes); shapes never change results.
+                         Default 1. */
   int full_system;    /* also build the paper's own iterative path on the global system
                          (Sec. 3-4; hps_full_apply, hps_full_precond, hps_full_solve): per
                          distinct homogenized constant the inverse Schur complement S~^{-1}, and
@@ -381,6 +385,18 @@ int hps_import_map(hps_handle* h, int what, int index, const double* host_in);
 #define HPS_INJECT_NONE 0
 #define HPS_INJECT_SKIP_ARRIVAL 1
 int hps_test_inject(hps_handle* h, int what, long long spin_limit);
+
+/* Launch shapes of a handle's batched GEMV kernels, per right-hand-side group
+ * (1, 2, <= 4, <= 8 per launch): matrix rows per warp pass (1, 2, 4, 8) and a
+ * cap on resident CTAs per SM (0 = the occupancy limit). */
+typedef struct {
+  int apply_rows_per_warp[2][4];   /* ItI apply with FP32 maps [0], FP64 maps [1] */
+  int apply_ctas_per_sm[2][4];
+  int stage_k_rows_per_warp[4];    /* preconditioner stage K, member groups of 1, 2, 4, 8 */
+  int stage_k_ctas_per_sm[4];
+  int tuned;                       /* 1 when chosen by the autotuner at setup */
+} hps_launch_shapes;
+int hps_get_launch_shapes(const hps_handle* h, hps_launch_shapes* out);
 
 /* Phases timed by the profiler (indices into hps_profile.ms / count). */
 #define HPS_PHASE_APPLY 0     /* w = A z inside the Arnoldi loop (working precision) */

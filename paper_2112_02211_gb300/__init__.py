@@ -92,7 +92,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, p, kappa, eta=None, b=None, forms=("fp64", "mixed"), restart=50,
                  cluster=2, maxit=5000, max_rhs=1, hbm_budget=0, device=0, precond_fp16=True, tc_apply=True,
-                 lean=False, lambda_bin=0.0, full_system=False):
+                 lean=False, lambda_bin=0.0, full_system=False, autotune=True):
         self.lib = N.load()
         self.nx, self.ny, self.nz, self.p, self.q = nx, ny, nz, p, p - 2
         self.nl = nx * ny * nz
@@ -117,6 +117,7 @@ class Solver:
         opt.lean = 1 if lean else 0
         opt.lambda_bin = float(lambda_bin)
         opt.full_system = 1 if full_system else 0
+        opt.autotune = 1 if autotune else 0
         self.n = self.ni + self.nb  # global-system unknowns per leaf
         bb = None
         if b is not None:
@@ -273,6 +274,16 @@ class Solver:
         if a.shape != (self.nb, self.nb):
             raise ValueError(f"R must be {self.nb} x {self.nb}")
         N.check(self.lib.hps_import_map(self.handle, N.HPS_EXPORT_R, index, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def launch_shapes(self):
+        """Rows per warp and CTAs per SM of the apply (FP32 maps, FP64 maps) and of stage K, per
+        right-hand-side group (1, 2, <=4, <=8), as chosen at setup."""
+        sh = N.LaunchShapes()
+        N.check(self.lib.hps_get_launch_shapes(self.handle, ctypes.byref(sh)))
+        return {"apply_rows_per_warp": [list(r) for r in sh.apply_rows_per_warp],
+                "apply_ctas_per_sm": [list(r) for r in sh.apply_ctas_per_sm],
+                "stage_k_rows_per_warp": list(sh.stage_k_rows_per_warp),
+                "stage_k_ctas_per_sm": list(sh.stage_k_ctas_per_sm), "tuned": bool(sh.tuned)}
 
     def profile(self, enable=None, reset=False):
         """Per-phase device times (ms) and kernel launch count since the last reset."""

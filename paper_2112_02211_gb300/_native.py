@@ -43,13 +43,19 @@ class Options(ctypes.Structure):
     _fields_ = [("forms", ctypes.c_int), ("restart", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("max_rhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
                 ("device", ctypes.c_int), ("precond_fp16", ctypes.c_int), ("tc_apply", ctypes.c_int),
-                ("lean", ctypes.c_int), ("lambda_bin", ctypes.c_double),
+                ("lean", ctypes.c_int), ("lambda_bin", ctypes.c_double), ("autotune", ctypes.c_int),
                 ("full_system", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("reorth_steps", ctypes.c_int)]
+
+
+class LaunchShapes(ctypes.Structure):
+    _fields_ = [("apply_rows_per_warp", (ctypes.c_int * 4) * 2), ("apply_ctas_per_sm", (ctypes.c_int * 4) * 2),
+                ("stage_k_rows_per_warp", ctypes.c_int * 4), ("stage_k_ctas_per_sm", ctypes.c_int * 4),
+                ("tuned", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -76,6 +82,7 @@ SIGNATURES = {
     "hps_export": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "hps_import_map": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "hps_test_inject": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
+    "hps_get_launch_shapes": (ctypes.c_int, [_P, ctypes.POINTER(LaunchShapes)]),
     "hps_full_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_full_precond": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hps_full_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_double, _P,

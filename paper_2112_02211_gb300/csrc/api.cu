@@ -208,6 +208,7 @@ void hps_default_options(hps_options* o) {
   o->tc_apply = 1;
   o->lean = 0;
   o->lambda_bin = 0.0;
+  o->autotune = 1;
   o->full_system = 0;
 }
 
@@ -345,6 +346,7 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
       if (fp16 && (r = build_precond_fp16(h, st))) return r;
     }
     if (o.full_system && (r = build_full_system(h, dc, st))) return r;
+    if (o.autotune && (r = autotune_shapes(h, st))) return r;
     HPS_CUDA_TRY(cudaStreamSynchronize(st));
     return HPS_OK;
   };
@@ -854,6 +856,24 @@ int hps_test_inject(hps_handle* h, int what, long long spin_limit) {
   h->test_skip_arrival = (what == HPS_INJECT_SKIP_ARRIVAL) ? 1 : 0;
   h->test_spin = spin_limit;
   krylov_drop_graph(h);  // a captured cycle would keep the old launch parameters
+  return HPS_OK;
+}
+
+int hps_get_launch_shapes(const hps_handle* h, hps_launch_shapes* out) {
+  if (!h || !out) {
+    set_error("hps_get_launch_shapes: bad arguments");
+    return HPS_EINVAL;
+  }
+  for (int k = 0; k < 2; ++k)
+    for (int g = 0; g < 4; ++g) {
+      out->apply_rows_per_warp[k][g] = h->shapes.apply[k][g].rpw;
+      out->apply_ctas_per_sm[k][g] = h->shapes.apply[k][g].bps;
+    }
+  for (int g = 0; g < 4; ++g) {
+    out->stage_k_rows_per_warp[g] = h->shapes.k[g].rpw;
+    out->stage_k_ctas_per_sm[g] = h->shapes.k[g].bps;
+  }
+  out->tuned = h->shapes.tuned ? 1 : 0;
   return HPS_OK;
 }
 

@@ -21,6 +21,9 @@
 // floats per lane per load), accumulates in the matrix's precision and
 // reduces with warp shuffles.
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
 
 template <class P, int NR, int RPW>
 cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm, cudaStream_t st, long long* counter,
-                       const int* gate) {
+                       const int* gate, int bps = 0) {
   using Acc = typename P::Acc;
   const size_t smem = ((size_t)NR * xcap + (size_t)NR * rowcap) * sizeof(Acc);
   auto kern = seg_gemv_kernel<P, NR, RPW>;
@@ -442,6 +445,7 @@ cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm,
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
   occ = std::max(occ, 1);
+  if (bps > 0) occ = std::min(occ, bps);  // a tuned cap on resident CTAs per SM
   long long grid = std::min<long long>(A.nitems, (long long)nsm * occ);
   if (grid <= 0) return cudaSuccess;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(A, xcap, rowcap, gate);
@@ -449,10 +453,39 @@ cudaError_t launch_one(const typename P::Args& A, int xcap, int rowcap, int nsm,
   return cudaGetLastError();
 }
 
-// Launch over right-hand-side groups of at most 8 (each group re-reads the matrix).
+// launch_one with the rows per warp chosen at run time (1, 2, 4 or 8; at most 16
+// accumulators of RPW rows x NR right-hand sides per thread, fewer rows otherwise)
+template <class P, int NR>
+cudaError_t launch_shaped(const typename P::Args& A, int xcap, int rowcap, int nsm, cudaStream_t st,
+                          long long* counter, const int* gate, LaunchShape sh) {
+  const int r = sh.rpw;
+  if constexpr (NR <= 2) {
+    if (r >= 8) return launch_one<P, NR, 8>(A, xcap, rowcap, nsm, st, counter, gate, sh.bps);
+  }
+  if constexpr (NR <= 4) {
+    if (r >= 4) return launch_one<P, NR, 4>(A, xcap, rowcap, nsm, st, counter, gate, sh.bps);
+  }
+  if (r >= 2) return launch_one<P, NR, 2>(A, xcap, rowcap, nsm, st, counter, gate, sh.bps);
+  return launch_one<P, NR, 1>(A, xcap, rowcap, nsm, st, counter, gate, sh.bps);
+}
+
+// group of nr right-hand sides -> index into the shape tables
+inline int group_index(int nr) { return nr == 1 ? 0 : nr == 2 ? 1 : nr <= 4 ? 2 : 3; }
+
+template <class P>
+cudaError_t launch_group(const typename P::Args& B, int nr, int xcap, int rowcap, int nsm, cudaStream_t st,
+                         long long* counter, const int* gate, LaunchShape sh) {
+  if (nr == 1) return launch_shaped<P, 1>(B, xcap, rowcap, nsm, st, counter, gate, sh);
+  if (nr == 2) return launch_shaped<P, 2>(B, xcap, rowcap, nsm, st, counter, gate, sh);
+  if (nr <= 4) return launch_shaped<P, 4>(B, xcap, rowcap, nsm, st, counter, gate, sh);
+  return launch_shaped<P, 8>(B, xcap, rowcap, nsm, st, counter, gate, sh);
+}
+
+// Launch over right-hand-side groups of at most 8 (each group re-reads the matrix);
+// shapes[g]: the launch shape of group index g.
 template <class P, class Shift>
 cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int xcap, int rowcap, cudaStream_t st,
-                          Shift shift) {
+                          Shift shift, const LaunchShape* shapes) {
   const int nsm = h->nsm;
   long long* counter = &h->prof.launches;
   for (int r0 = 0; r0 < nrhs; r0 += 8) {
@@ -460,11 +493,7 @@ cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int
     const int nr = std::min(8, nrhs - r0);
     shift(B, r0);
     B.nrhs = nr;
-    cudaError_t e;
-    if (nr == 1) e = launch_one<P, 1, 4>(B, xcap, rowcap, nsm, st, counter, h->gate);
-    else if (nr == 2) e = launch_one<P, 2, 4>(B, xcap, rowcap, nsm, st, counter, h->gate);
-    else if (nr <= 4) e = launch_one<P, 4, 2>(B, xcap, rowcap, nsm, st, counter, h->gate);
-    else e = launch_one<P, 8, 1>(B, xcap, rowcap, nsm, st, counter, h->gate);
+    const cudaError_t e = launch_group<P>(B, nr, xcap, rowcap, nsm, st, counter, h->gate, shapes[group_index(nr)]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -494,11 +523,12 @@ cudaError_t apply_t(const hps_handle* h, const TM* R, const TIN* f, TOUT* y, con
   A.nf = h->nf;
   A.nrhs = nrhs;
   A.nitems = (long long)h->nl * 6;
+  const LaunchShape* shapes = h->shapes.apply[std::is_same<TM, double2>::value ? 1 : 0];
   return launch_groups<P>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename P::Args& B, int r0) {
     B.f += (long long)r0 * h->nf;
     B.y += (long long)r0 * h->nf;
     if (B.bvec) B.bvec += (long long)r0 * h->nf;
-  });
+  }, shapes);
 }
 
 template <class TM, class TIN, class TOUT>
@@ -592,10 +622,7 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
         A.items = h->dct.kitems[g];
         A.nitems = n;
         A.nrhs = 1 << g;
-        if (g == 0) e = launch_one<P, 1, 4>(A, xcap, q2, h->nsm, st, counter, h->gate);
-        else if (g == 1) e = launch_one<P, 2, 4>(A, xcap, q2, h->nsm, st, counter, h->gate);
-        else if (g == 2) e = launch_one<P, 4, 2>(A, xcap, q2, h->nsm, st, counter, h->gate);
-        else e = launch_one<P, 8, 2>(A, xcap, q2, h->nsm, st, counter, h->gate);
+        e = launch_group<P>(A, 1 << g, xcap, q2, h->nsm, st, counter, h->gate, h->shapes.k[g]);
       }
     }
     h->prof.end(HPS_PHASE_PRECOND_K, ev, st);
@@ -666,11 +693,12 @@ cudaError_t rhs_t(const hps_handle* h, const TM* H, const double2* s, const doub
   A.nint = h->nint;
   A.nrhs = nrhs;
   A.nitems = (long long)h->nl * 6;
+  static const LaunchShape kDefault[4] = {{4, 0}, {4, 0}, {2, 0}, {1, 0}};
   return launch_groups<P>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename P::Args& B, int r0) {
     if (B.s) B.s += (long long)r0 * h->nint;
     if (B.t) B.t += (long long)r0 * h->nf;
     B.out += (long long)r0 * h->nf;
-  });
+  }, kDefault);
 }
 
 cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
@@ -708,6 +736,153 @@ cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, con
     return precond_t(h, h->B32, h->Kc32, (const float4*)r, (float2*)z, (float2*)scratch, nrhs, st, nullptr, nullptr,
                      tc);
   return precond_t(h, h->B32, h->Kc32, (const double2*)r, (float2*)z, (float2*)scratch, nrhs, st, nullptr, nullptr, tc);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the launch shapes (rows per warp, resident CTAs per SM) of the
+// batched GEMV kernels, run once per shape at setup: every candidate is timed
+// with CUDA events (one warm-up launch, then three) on the handle's own data,
+// the fastest kept in a process-wide table keyed by (device, kernel, q,
+// leaves, right-hand-side group, work items), so later handles of the same
+// size reuse it.  The shapes do not change results (see LaunchShape).
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::array<long long, 6>, LaunchShape> g_tuned;
+
+template <class P>
+LaunchShape tune_group(const hps_handle* h, const typename P::Args& A, int nr, int xcap, int rowcap,
+                       const std::array<long long, 6>& key, LaunchShape dflt, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return dflt;
+  }
+  long long dummy = 0;
+  auto time_one = [&](LaunchShape sh) -> float {
+    if (launch_group<P>(A, nr, xcap, rowcap, h->nsm, st, &dummy, nullptr, sh) != cudaSuccess) return 1e30f;
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < 3; ++i)
+      if (launch_group<P>(A, nr, xcap, rowcap, h->nsm, st, &dummy, nullptr, sh) != cudaSuccess) return 1e30f;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / 3.f;
+  };
+  LaunchShape best = dflt;
+  float tbest = time_one(dflt);
+  const int rmax = nr <= 2 ? 8 : nr <= 4 ? 4 : 2;
+  for (int rpw = 1; rpw <= rmax; rpw *= 2)
+    for (int bps = 0; bps <= 3; ++bps) {
+      const LaunchShape sh{rpw, bps};
+      if (sh.rpw == dflt.rpw && sh.bps == dflt.bps) continue;
+      const float t = time_one(sh);
+      if (t < 0.98f * tbest) {  // a clear win over the incumbent only
+        tbest = t;
+        best = sh;
+      }
+    }
+  cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[key] = best;
+  return best;
+}
+
+template <class TM, class TIN, class TOUT>
+cudaError_t tune_apply(hps_handle* h, const TM* R, int kind, void* fbuf, void* ybuf, int nr, cudaStream_t st) {
+  using P = ApplyP<TM, TIN, TOUT>;
+  typename P::Args A;
+  A.R = R;
+  A.ldR = h->ldR;
+  A.nb = h->nb;
+  A.q2 = h->q * h->q;
+  A.g = GridDims{h->nx, h->ny, h->nz};
+  A.f = (const TIN*)fbuf;
+  A.y = (TOUT*)ybuf;
+  A.bvec = nullptr;
+  A.nf = h->nf;
+  A.nrhs = nr;
+  A.nitems = (long long)h->nl * 6;
+  const int g = group_index(nr);
+  const std::array<long long, 6> key{h->dev, kind, h->q, h->nl, nr, A.nitems};
+  h->shapes.apply[kind][g] = tune_group<P>(h, A, nr, xcap_of(h), A.q2, key, h->shapes.apply[kind][g], st);
+  return cudaSuccess;
+}
+
+template <class TM>
+cudaError_t tune_stage_k(hps_handle* h, const TM* K, const float* kscale, void* t, void* z, bool tc, cudaStream_t st) {
+  using P = PrecKP<TM, float2, float2>;
+  typename P::Args A;
+  A.K = K;
+  A.kscale = kscale;
+  A.kc_off = h->dct.kc_off;
+  A.kc_slot_begin = h->dct.kc_slot_begin;
+  A.members = h->dct.kc_members;
+  A.cl_slot_begin = h->dct.cl_slot_begin;
+  A.slot_lf = h->dct.slot_lf;
+  A.cl_tpos = h->dct.cl_tpos;
+  A.nb = h->nb;
+  A.q2 = h->q * h->q;
+  A.nf = h->nf;
+  A.tstride = h->ct.tsize;
+  A.t = (const float2*)t;
+  A.z = (float2*)z;
+  for (int g = 0; g < 4; ++g) {
+    const long long n = tc ? h->ct.kitems_ntc[g] : (long long)h->ct.kitems[g].size();
+    if (n == 0) continue;
+    A.items = h->dct.kitems[g];
+    A.nitems = n;
+    A.nrhs = 1 << g;
+    const std::array<long long, 6> key{h->dev, 10 + (long long)sizeof(TM), h->q, h->nl, g, n};
+    h->shapes.k[g] = tune_group<P>(h, A, 1 << g, xcap_of(h), A.q2, key, h->shapes.k[g], st);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int autotune_shapes(hps_handle* h, cudaStream_t st) {
+  const long long nf = h->nf;
+  const int nr_max = std::min(8, std::max(1, h->opt.max_rhs));
+  void *fbuf = nullptr, *ybuf = nullptr;
+  const size_t bytes = (size_t)nr_max * nf * sizeof(double2);
+  if (cudaMalloc(&fbuf, bytes) != cudaSuccess || cudaMalloc(&ybuf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (fbuf) cudaFree(fbuf);
+    return HPS_OK;  // tuning is an optimization: keep the default shapes
+  }
+  cudaMemsetAsync(fbuf, 0, bytes, st);
+  cudaMemsetAsync(ybuf, 0, bytes, st);
+  std::vector<int> groups{1};
+  if (nr_max > 1) groups.push_back(nr_max);
+  for (int nr : groups) {
+    // the inner apply of each form: complex-FP32 operand into the double-float basis, and FP64
+    if (h->R32) tune_apply<float2, float2, float4>(h, h->R32, 0, fbuf, ybuf, nr, st);
+    if (h->R64) tune_apply<double2, double2, double2>(h, h->R64, 1, fbuf, ybuf, nr, st);
+  }
+  // SIMT stage K of the mixed solve (FP16 blocks when kept, else FP32)
+  if (h->has_precond && h->ct.nslots > 0 && h->pc_scratch) {
+    cudaMemsetAsync(h->pc_scratch, 0, (size_t)h->ct.tsize * sizeof(float2), st);
+    const bool tc = h->opt.tc_apply && h->Kc32 && h->tc_error && !h->ct.kc_tc.empty();
+    if (h->Kc16) tune_stage_k<__half2>(h, h->Kc16, h->Kc16s, h->pc_scratch, ybuf, tc, st);
+    else if (h->Kc32) tune_stage_k<float2>(h, h->Kc32, nullptr, h->pc_scratch, ybuf, tc, st);
+  }
+  cudaStreamSynchronize(st);
+  cudaGetLastError();
+  cudaFree(fbuf);
+  cudaFree(ybuf);
+  h->shapes.tuned = true;
+  return HPS_OK;
 }
 
 }  // namespace hps

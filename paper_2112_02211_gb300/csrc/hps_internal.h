@@ -141,6 +141,23 @@ struct DeviceClusterTables {
   int* pos_class = nullptr;
 };
 
+// Launch shape of the batched GEMV kernels: matrix rows per warp pass and a cap on
+// resident CTAs per SM (0 = the occupancy limit).  Neither changes any result: each
+// row is one warp's sum over its lanes in the same order.
+struct LaunchShape {
+  int rpw = 4;
+  int bps = 0;
+};
+// The shapes a handle launches with, per right-hand-side group (1, 2, <= 4, <= 8):
+// the ItI apply with FP32 maps [0] and FP64 maps [1], and the SIMT stage K per
+// member-group width (1, 2, 4, 8).  Defaults from a hand sweep; replaced at setup
+// by the autotuner (options.autotune).
+struct Shapes {
+  LaunchShape apply[2][4] = {{{4, 0}, {4, 0}, {2, 0}, {1, 0}}, {{4, 0}, {4, 0}, {2, 0}, {1, 0}}};
+  LaunchShape k[4] = {{4, 0}, {4, 0}, {2, 0}, {2, 0}};
+  bool tuned = false;
+};
+
 // Per-phase CUDA-event timing and a launch counter (see hps_profile).  Events
 // are recorded as external events, so an interval recorded while a stream is
 // being captured becomes a pair of event nodes of the graph; such intervals
@@ -349,6 +366,7 @@ struct hps_handle {
   // (apply, preconditioner) read first, returning at once when it is 0 (no
   // right-hand side still active).  nullptr otherwise.
   mutable const int* gate = nullptr;
+  hps::Shapes shapes;
   // test hook of hps_test_inject: bounded-wait limit (tries) of the tensor-core apply (0 =
   // default) and whether one of its CTAs skips one mbarrier arrival
   long long test_spin = 0;
@@ -410,6 +428,9 @@ cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, con
 // float or double-float; nrhs a multiple of 64.
 // whether launch_apply runs nrhs right-hand sides with complex-FP32 input on the tensor cores
 bool apply_tc_eligible(const hps_handle* h, int nrhs);
+// Times the candidate launch shapes of the applies and the SIMT stage K the solves will use
+// and keeps the fastest in h->shapes (process-wide cache keyed by kernel, device and sizes).
+int autotune_shapes(hps_handle* h, cudaStream_t st);
 cudaError_t launch_apply_tc(const hps_handle* h, const float2* f, void* y, bool out_df, int nrhs, int* d_error,
                             cudaStream_t st);
 // Stage K of the preconditioner for the shared K blocks listed in ct.kc_tc, on
