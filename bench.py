@@ -51,14 +51,17 @@ def parse():
     ap.add_argument("--L", type=int, default=16, help="leaves per axis (16 = the benchmark workload)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / no-preconditioner comparison runs")
     ap.add_argument("--cpu-sample-L", type=int, default=4)
-    ap.add_argument("--serving-requests", type=int, default=8,
-                    help="requests of the scaled serving stream timed after the solves (0 = skip)")
+    ap.add_argument("--serving-requests", type=int, default=10,
+                    help="requests of the serving stream timed after the solves (0 = skip)")
     ap.add_argument("--lambda-bin", type=float, default=0.01,
                     help="bin width of the homogenized constants, relative to max |lambda| (0 = per-leaf)")
     ap.add_argument("--no-full-system", action="store_true",
                     help="skip the comparison solve of the paper's global-system path")
-    ap.add_argument("--no-unbinned", action="store_true",
-                    help="skip the comparison solve with per-leaf (unbinned) preconditioner blocks")
+    ap.add_argument("--unbinned", action="store_true",
+                    help="also time the solve with per-leaf (unbinned) preconditioner blocks")
+    ap.add_argument("--configs", default="multi_rhs,large",
+                    help="full-size configurations timed after the headline (comma list of multi_rhs, large; "
+                         "'' = none)")
     return ap.parse_args()
 
 
@@ -312,7 +315,7 @@ def run_gpu(args, dist):
                     torch.linalg.norm(f_mixed - out).item() / torch.linalg.norm(out).item())
 
     # per-leaf (unbinned) preconditioner blocks, mixed form, for comparison
-    if not args.no_compare and not args.no_unbinned and args.lambda_bin > 0:
+    if not args.no_compare and args.unbinned and args.lambda_bin > 0:
         solver.close()
         solver = hps.Solver(L, L, L, p, kappa=w.kappa, eta=w.eta, b=b, device=dist.local, forms=("mixed",))
         c_ms, c_infos, c_prof, _ = timed("mixed", True, 1, 1, profile=True)
@@ -422,26 +425,159 @@ def run_gpu(args, dist):
     solver.close()
     if args.serving_requests > 0:
         rec["serving"] = run_serving(args, dist)
+    extra = [c for c in args.configs.split(",") if c]
+    if extra:
+        rec["configurations"] = {}
+        for name in extra:
+            rec["configurations"][name] = run_config(name, dist)
     return rec
 
 
-def run_serving(args, dist):
-    """A bounded, scaled sample of the serving stream: Poisson arrivals at 20/s, grids of
-    4^3-6^3 leaves, p in {8, 10}, kappa in [20, 60], 3-8 bumps, 1-16 sources; mixed form,
-    tol 1e-6, admission by an HBM budget of 64 GiB, up to 4 requests in flight.
-    Latency = arrival to result on the host, including each request's setup (its own
-    medium, so its own leaf maps)."""
-    from paper_2112_02211_gb300.serving import HPSBackend, Request, Server, latency_stats
+def tf32_peak():
+    """Dense TF32 tensor peak for the tensor-core kernels: the measured BF16 burst figure times
+    the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s dense)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops"]) * (1.1 / 2.25), "measured bf16 x nominal tf32/bf16"
+    except Exception:
+        return 1900.0 * (1.1 / 2.25), "fallback bf16 x nominal tf32/bf16"
 
-    ws = W.serving_stream(n=args.serving_requests, rate=20.0, seed=7, L_range=(4, 6), p_choices=(8, 10),
-                          kappa_range=(20.0, 60.0), max_sources=16)
-    reqs = [Request(i, w, w.meta["arrival"]) for i, w in enumerate(ws)]
-    srv = Server(HPSBackend(form="mixed", device=dist.local), hbm_budget=64 << 30, max_active=4)
+
+def run_config(name, dist):
+    """One full-size configuration in its own form (lean mixed, 2x2x2 cluster blocks binned at
+    0.01), inputs resident in HBM, CUDA events around `steps` solves after one warm-up:
+    * multi_rhs: 16^3 leaves, p = 12, kappa = 60, five bumps, 64 Gaussian sources, tol 1e-6,
+      GMRES(50) (30 if the basis does not fit); apply and stage K of the 64 right-hand sides on
+      the tensor cores;
+    * large: 32^3 leaves, p = 10, kappa = 200, smooth random complex medium, tol 1e-5, GMRES(50).
+    Unknowns/s counts face unknowns over all right-hand sides."""
+    import torch
+
+    import paper_2112_02211_gb300 as hps
+
+    if name == "multi_rhs":
+        w, nrhs, steps = W.multi_rhs_16cubed(), 64, 2
+    elif name == "large":
+        w, nrhs, steps = W.large_32cubed(), 1, 3
+    else:
+        return {"error": f"unknown configuration {name}"}
+    L, p, q = w.nx, w.p, w.q
+    xi, xf = hps.nodes(L, L, L, p)
+    s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
+    b = w.sample_b(xi)
+    solver, restart, setup_s = None, None, None
+    for m in (50, 30):
+        try:
+            t0 = time.time()
+            solver = hps.Solver(L, L, L, p, kappa=w.kappa, eta=w.eta, b=b, forms=("mixed",), lean=True,
+                                lambda_bin=0.01, max_rhs=nrhs, restart=m, device=dist.local)
+            torch.cuda.synchronize()
+            setup_s = time.time() - t0
+            out = torch.empty(nrhs * solver.nf, dtype=torch.complex128, device="cuda")
+            solver.solve(s=s, tol=w.tol, form="mixed", nrhs=nrhs, out=out)  # warm-up; allocates the basis
+            restart = m
+            break
+        except hps.HPSError as e:
+            if solver is not None:
+                solver.close()
+                solver = None
+            torch.cuda.empty_cache()
+            if m == 30:
+                return {"error": str(e)}
+    try:
+        stream = torch.cuda.current_stream()
+        solver.profile(enable=True, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            _, info = solver.solve(s=s, tol=w.tol, form="mixed", nrhs=nrhs, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = solver.profile(enable=False, reset=True)
+        ncl, k_blocks, b_blocks = solver.precond_info()
+        mem = solver.memory_bytes
+        nf = solver.nf
+    finally:
+        solver.close()
+    pk, pk_src = peaks()
+    tpk, tpk_src = tf32_peak()
+    nb = 6 * q * q
+    rows = interior_face_pairs(L) * q * q  # rows of R whose output is used
+    nint = 24 * q * q
+    roof = {}
+
+    def entry(phase, by, flops=None, tensor=False):
+        cnt = prof["count"][phase]
+        if not cnt:
+            return
+        dur = prof["ms"][phase] / cnt / 1e3
+        e = {"avg_launch_ms": round(dur * 1e3, 4), "launches": cnt, "algorithmic_bytes": by,
+             "achieved_gbs": round(by / dur / 1e9, 1), "hbm_peak_gbs": pk, "hbm_frac": round(by / dur / 1e9 / pk, 4)}
+        if flops:
+            e["algorithmic_flops"] = flops
+            e["achieved_tflops"] = round(flops / dur / 1e12, 1)
+            if tensor:
+                e["tf32_peak_tflops"] = round(tpk, 1)
+                e["tensor_frac"] = round(flops / dur / 1e12 / tpk, 4)
+            # the roofline is the larger of the two time bounds
+            t_bound = max(by / (pk * 1e9), (flops / (tpk * 1e12)) if tensor else 0.0)
+            e["bound"] = "tensor" if tensor and flops / (tpk * 1e12) > by / (pk * 1e9) else "hbm"
+            e["frac_of_bound"] = round(t_bound / dur, 4)
+        else:
+            e["bound"] = "hbm"
+        roof[phase] = e
+
+    if nrhs >= 64:
+        # three TF32 products of R (n_b x 2 n_b real) against 128 real columns per 64 RHS
+        a_flops = 3 * 2.0 * rows * (2 * nb) * (2 * nrhs)
+        a_bytes = rows * nb * 8 + nrhs * nf * (8 + 8 + 16)
+        entry("apply", a_bytes, a_flops, tensor=True)
+        # stage K: one TF32 product of every K_c (n_int x 2 n_int real) against 128 real columns per
+        # 64 RHS for each member cluster
+        k_flops = 2.0 * ncl * nint * (2 * nint) * (2 * nrhs)
+        k_bytes = k_blocks * nint * nint * 8 + ncl * nint * 2 * 8 * nrhs
+        entry("precond_k", k_bytes, k_flops, tensor=True)
+    else:
+        entry("apply", apply_bytes(L, q, 8, 8, 16))
+        kb, bb = precond_bytes(L, q, 4, 8, in_bytes=16, scale_bytes=4, k_blocks=k_blocks, b_blocks=b_blocks)
+        entry("precond_k", kb)
+        entry("precond_b", bb)
+    return {"workload": w.name, "leaves": L ** 3, "p": p, "q": q, "kappa": w.kappa, "tol": w.tol, "nrhs": nrhs,
+            "restart": restart, "form": "lean mixed (FP32 maps + FP16 remainders, FP16/FP32 cluster blocks)",
+            "setup_s": round(setup_s, 1), "device_bytes": mem, "precond_blocks": [ncl, k_blocks, b_blocks],
+            "steps": steps, "ms_per_solve": ms, "unknowns_per_s": nrhs * nf / (ms / 1e3),
+            "iterations": info["iterations"], "cycles": info["cycles"], "rel_residual": info["rel_residual"],
+            "converged": info["converged"], "reorth_steps": info["reorth_steps"],
+            "phase_ms_per_solve": {k: round(v / steps, 3) for k, v in prof["ms"].items()},
+            "gpu_launches_per_solve": prof["launches"] // steps, "roofline": roof, "peak_sources": [pk_src, tpk_src]}
+
+
+def run_serving(args, dist):
+    """A stated subset of the serving stream, unshrunk: the stream of 500 requests as generated
+    (Poisson arrivals at 20/s, seed 7; per request L ~ U{8..24} leaves per axis, p in {8, 10, 12},
+    kappa ~ U[20, 120], 3-8 bumps, 1-16 Gaussian sources), of which the first
+    `--serving-requests` with p = 8 are served at their own sizes and arrival times (the p = 10
+    and 12 requests need 10 s to 11 min of FP64 leaf elimination each, more than a benchmark run
+    can hold).  Mixed form, tol 1e-6, 2x2x2 clusters binned at 0.01, admission by an HBM budget
+    of 96 GiB, up to 4 requests in flight.  Latency = arrival to result on the host, including
+    queueing and each request's setup (its own medium, so its own leaf maps)."""
+    from paper_2112_02211_gb300.serving import HPSBackend, Request, Server, latency_stats, overlapping_pairs
+
+    ws = W.serving_stream(n=500, rate=20.0, seed=7)
+    picked = [(i, w) for i, w in enumerate(ws) if w.p == 8][:args.serving_requests]
+    reqs = [Request(i, w, w.meta["arrival"]) for i, w in picked]
+    srv = Server(HPSBackend(form="mixed", device=dist.local, lambda_bin=0.01), hbm_budget=96 << 30, max_active=4)
     res = srv.run(reqs)
     st = latency_stats(res)
-    st.update({"requests": len(reqs), "peak_active": srv.peak_active, "peak_budget_bytes": srv.peak_bytes,
-               "stream": "serving recipe scaled to 4^3-6^3 leaves, p in {8,10}, kappa in [20,60]; "
-                         "latency includes per-request setup"})
+    st.update({"requests": len(reqs), "stream_indices": [i for i, _ in picked],
+               "grids": [f"{w.nx}^3 p={w.p} kappa={w.kappa:.1f} nrhs={w.nrhs}" for _, w in picked],
+               "peak_active": srv.peak_active, "peak_budget_bytes": srv.peak_bytes,
+               "overlapping_pairs": len(overlapping_pairs(res)),
+               "errors": [r.error for r in res if r.error],
+               "stream": "serving stream (500 requests, seed 7) as generated; its first p = 8 requests at their "
+                         "own sizes and arrival times; latency includes queueing and per-request setup"})
     return st
 
 
@@ -478,12 +614,52 @@ def oracle_sample(L_sample, steps=1, warmup=0, min_seconds=0.0):
     return g.nf / dt, dt, cores, n
 
 
+def oracle_apply_rate(L_sample, reps=5):
+    """The oracle's apply (I + Pi R) f on the sample grid (its own FP64 maps), in GB/s of the same
+    algorithmic bytes the GPU apply is credited with (rows of R with a neighbour, f read twice,
+    y written; complex double)."""
+    import oracle as O
+
+    w = W.scaled(W.bump_16cubed(), L_sample)
+    g = O.Grid(L_sample, L_sample, L_sample, w.p)
+    xi = O.interior_nodes(g)
+    prob = O.build_problem(g, w.kappa, w.eta, w.sample_b(xi))
+    f = np.random.default_rng(0).standard_normal(g.nf) + 0j
+    O.apply_face(g, prob.R, f)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        O.apply_face(g, prob.R, f)
+    dt = (time.perf_counter() - t0) / reps
+    return apply_bytes(L_sample, w.q, 16, 16, 16) / dt / 1e9, dt
+
+
+def single_core_sample(L_sample):
+    """The oracle sample in a child process with BLAS and OpenMP limited to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "v, dt, c, n = bench.oracle_sample(%d, steps=1, warmup=0); print(json.dumps([v, dt, n]))" % (ROOT, L_sample))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        v, dt, n = json.loads(r.stdout.strip().splitlines()[-1])
+        return v, dt
+    except Exception:
+        return None, None
+
+
 def cpu_baseline_record(L_sample):
     v, dt, cores, n = oracle_sample(L_sample, steps=3, warmup=1, min_seconds=10.0)
+    v1, dt1 = single_core_sample(L_sample)
+    gbs, adt = oracle_apply_rate(L_sample)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"bump workload scaled to {L_sample}^3 leaves (same p, kappa, medium, source): "
                       f"oracle RHS build + GMRES(50) to 1e-6, no preconditioner, setup excluded; "
-                      f"{n} solves of {dt:.2f} s; numpy with its default BLAS threading"}
+                      f"{n} solves of {dt:.2f} s; numpy with its default BLAS threading",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": "the same sample, BLAS and OpenMP limited to one thread",
+                            "seconds_per_solve": dt1},
+            "apply": {"achieved_gbs": round(gbs, 2), "seconds_per_apply": adt, "cores": cores,
+                      "sample": f"oracle (I + Pi R) f on the {L_sample}^3 sample's FP64 maps, algorithmic "
+                                f"bytes as for the GPU apply (complex double)"}}
 
 
 def run_reference(args, dist):

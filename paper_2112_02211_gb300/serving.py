@@ -23,7 +23,7 @@ from typing import Any, Callable, List, Optional
 
 import numpy as np
 
-__all__ = ["Request", "Result", "Server", "HPSBackend", "latency_stats"]
+__all__ = ["Request", "Result", "Server", "HPSBackend", "latency_stats", "overlapping_pairs"]
 
 
 @dataclass
@@ -50,12 +50,19 @@ class Result:
 
 
 class HPSBackend:
-    """Runs one request through the CUDA library on the calling thread's own stream."""
+    """Runs one request through the CUDA library on the calling thread's own stream.  Per request
+    it reports the setup and solve times (host clock) and the request's interval on the device
+    timeline: CUDA events on its stream at the start and the end of its work, read against one
+    epoch event of the backend, so that intervals of different requests can be compared."""
 
-    def __init__(self, form="mixed", device=0, precond=True):
+    def __init__(self, form="mixed", device=0, precond=True, lean=False, lambda_bin=0.0):
         self.form = form
         self.device = device
         self.precond = precond
+        self.lean = lean
+        self.lambda_bin = lambda_bin
+        self._epoch = None
+        self._lock = threading.Lock()
 
     def bytes_needed(self, w):
         import ctypes
@@ -67,19 +74,37 @@ class HPSBackend:
         o.forms = N.HPS_FORM_MIXED if self.form == "mixed" else N.HPS_FORM_FP64
         o.max_rhs = w.nrhs
         o.device = self.device
+        o.lean = 1 if self.lean else 0
+        o.lambda_bin = self.lambda_bin
         g = N.Grid(w.nx, w.ny, w.nz, w.p, w.p - 2)
         return int(lib.hps_setup_bytes(ctypes.byref(g), ctypes.byref(o), w.nrhs))
+
+    def epoch(self):
+        import torch
+        with self._lock:
+            if self._epoch is None:
+                torch.cuda.set_device(self.device)
+                self._epoch = torch.cuda.Event(enable_timing=True)
+                self._epoch.record(torch.cuda.current_stream(self.device))
+        return self._epoch
 
     def run(self, w):
         import torch
 
         from . import Solver, face_normals, nodes
         torch.cuda.set_device(self.device)
+        epoch = self.epoch()
         stream = torch.cuda.Stream(device=self.device)
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
         xi, xf = nodes(w.nx, w.ny, w.nz, w.p)
         with torch.cuda.stream(stream):
+            e_start.record(stream)
+            t0 = time.perf_counter()
             solver = Solver(w.nx, w.ny, w.nz, w.p, kappa=w.kappa, eta=w.eta, b=w.sample_b(xi),
-                            forms=(self.form,), max_rhs=w.nrhs, device=self.device)
+                            forms=(self.form,), max_rhs=w.nrhs, device=self.device, lean=self.lean,
+                            lambda_bin=self.lambda_bin)
+            t1 = time.perf_counter()
             try:
                 s = w.sample_s(xi)
                 t = None
@@ -91,7 +116,28 @@ class HPSBackend:
                                        nrhs=w.nrhs, out=out, stream=stream, precond=self.precond)
             finally:
                 solver.close()
+            e_end.record(stream)
+        e_end.synchronize()
+        info = dict(info)
+        info["setup_s"] = t1 - t0
+        info["solve_s"] = time.perf_counter() - t1
+        epoch.synchronize()
+        info["device_interval_ms"] = (epoch.elapsed_time(e_start), epoch.elapsed_time(e_end))
         return out, info
+
+
+def overlapping_pairs(results):
+    """Pairs of requests whose device intervals intersect (their work was on the GPU at the
+    same time)."""
+    iv = [(r.rid, r.info.get("device_interval_ms")) for r in results if r.error is None and r.info]
+    iv = [(rid, x) for rid, x in iv if x]
+    out = []
+    for i in range(len(iv)):
+        for j in range(i + 1, len(iv)):
+            (a, (a0, a1)), (b, (b0, b1)) = iv[i], iv[j]
+            if max(a0, b0) < min(a1, b1):
+                out.append((a, b))
+    return out
 
 
 class Server:
@@ -173,10 +219,17 @@ class Server:
 
 
 def latency_stats(results: List[Result]):
+    """p50/p99 latency (arrival to result), throughput, and the median queue, setup and solve
+    time per request (setup and solve as the backend reports them)."""
     ok = [r for r in results if r.error is None]
     lat = np.array([r.latency for r in ok]) if ok else np.zeros(0)
     span = (max(r.done for r in ok) - min(r.arrival for r in ok)) if ok else 0.0
     unknowns = sum(r.f.size for r in ok if r.f is not None)
+
+    def med(vals):
+        vals = [v for v in vals if v is not None]
+        return float(np.median(vals)) if vals else None
+
     return {
         "completed": len(ok),
         "failed": len(results) - len(ok),
@@ -186,4 +239,7 @@ def latency_stats(results: List[Result]):
         "solves_per_s": len(ok) / span if span > 0 else None,
         "unknowns_per_s": unknowns / span if span > 0 else None,
         "makespan_s": span,
+        "queue_s_p50": med([r.admitted - r.arrival for r in ok]),
+        "setup_s_p50": med([(r.info or {}).get("setup_s") for r in ok]),
+        "solve_s_p50": med([(r.info or {}).get("solve_s") for r in ok]),
     }

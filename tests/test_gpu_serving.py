@@ -9,7 +9,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import workloads as W  # noqa: E402
-from paper_2112_02211_gb300.serving import HPSBackend, Request, Server, latency_stats  # noqa: E402
+from paper_2112_02211_gb300.serving import HPSBackend, Request, Server, latency_stats, overlapping_pairs  # noqa: E402
 
 
 def _stream():
@@ -25,7 +25,10 @@ def test_alone_equals_in_the_mix(form):
     alone = Server(be, hbm_budget=64 << 30, max_active=1).run(reqs)
     mixed_srv = Server(be, hbm_budget=64 << 30, max_active=4)
     mixed = mixed_srv.run(reqs)
-    assert mixed_srv.peak_active > 1, "requests did not overlap"
+    assert mixed_srv.peak_active > 1, "requests were not admitted together"
+    # their device work overlapped in time: CUDA-event intervals of two requests intersect
+    assert overlapping_pairs(mixed), [r.info.get("device_interval_ms") for r in mixed]
+    assert not overlapping_pairs(alone)
     for a, m in zip(alone, mixed):
         assert a.error is None and m.error is None, (a.error, m.error)
         assert a.info["converged"] and m.info["converged"]
