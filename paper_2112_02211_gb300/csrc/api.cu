@@ -282,8 +282,11 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
     if (!o.lean && (r = dalloc(h, (void**)&h->R64, rel * sizeof(double2)))) return r;
     if (want32 && (r = dalloc(h, (void**)&h->R32, rel * sizeof(float2)))) return r;
     if (!o.lean && (r = dalloc(h, (void**)&h->H64, hel * sizeof(double2)))) return r;
-    if (o.lean && (r = dalloc(h, (void**)&h->H32, hel * sizeof(float2)))) return r;
-    if (o.lean) {
+    // complex-FP32 H and the FP16 remainders of the FP32 maps (compensated maps, compensated.cu):
+    // lean mode's only accurate maps, and the mixed form's fast restart residual and right-hand
+    // side at tolerances >= 1e-8
+    if (want32 && (r = dalloc(h, (void**)&h->H32, hel * sizeof(float2)))) return r;
+    if (want32) {
       if ((r = dalloc(h, (void**)&h->R16lo, rel * sizeof(__half2)))) return r;
       if ((r = dalloc(h, (void**)&h->R16ls, (size_t)h->nl * h->nb * sizeof(float)))) return r;
       if ((r = dalloc(h, (void**)&h->H16lo, hel * sizeof(__half2)))) return r;
@@ -378,8 +381,8 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
   const size_t hel = (size_t)h.nl * h.nb * h.ldH;
   size_t bytes = h.tl.total * sizeof(double) + (o.lean ? 0 : rel * c16) + (want32 ? rel * c8 : 0) +
                  hel * (o.lean ? c8 : c16) + (size_t)h.nl * c16;
-  if (o.lean)  // FP16 remainders of R and H and their row scales
-    bytes += (rel + hel) * sizeof(__half2) + (size_t)2 * h.nl * h.nb * sizeof(float);
+  if (want32)  // FP16 remainders of R and H and their row scales; FP32 H beside FP64 H
+    bytes += (rel + hel) * sizeof(__half2) + (size_t)2 * h.nl * h.nb * sizeof(float) + (o.lean ? 0 : hel * c8);
   const int q2 = h.q * h.q;
   size_t nslots = 0, tsize = 1;
   if (o.cluster == 2) {
@@ -647,9 +650,12 @@ int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, i
     HPS_CUDA_TRY(cudaMemcpyAsync(k.t_dev, t, (size_t)nrhs * h->nf * sizeof(double2), cudaMemcpyHostToDevice, st));
     td = k.t_dev;
   }
+  // the compensated FP32 maps reproduce the FP64 ones to ~3e-11: the mixed form uses them for the
+  // right-hand side and the restart residual when the tolerance is at least 1e-8
+  const bool cf = form == HPS_FORM_MIXED && tol >= kCompensatedMinTol && h->R16lo && h->H16lo;
   {
     cudaEvent_t ev = h->prof.begin(st);
-    HPS_CUDA_TRY(launch_rhs(h, sd, td, k.b, nrhs, st));
+    HPS_CUDA_TRY(launch_rhs(h, sd, td, k.b, nrhs, st, cf || !h->H64));
     h->prof.end(HPS_PHASE_RHS, ev, st);
   }
   const bool fdev = is_device_ptr(f_out);

@@ -702,7 +702,8 @@ cudaError_t rhs_t(const hps_handle* h, const TM* H, const double2* s, const doub
 }
 
 cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool compensated) {
+  if (compensated && h->H16lo && h->H32) return launch_rhs_cf(h, s, t, b, nrhs, st);
   if (h->H64) return rhs_t(h, h->H64, s, t, b, nrhs, st);
   if (h->H16lo) return launch_rhs_cf(h, s, t, b, nrhs, st);
   return rhs_t(h, h->H32, s, t, b, nrhs, st);

@@ -420,8 +420,12 @@ enum class VType { C128, C64, DF };
 cudaError_t launch_apply(const hps_handle* h, bool fp32_matrix, VType tin, const void* f,
                          VType tout, void* y, const double2* bvec, int nrhs, bool residual,
                          cudaStream_t st);
+// compensated: the FP32 maps with their FP16 remainders (when kept) instead of the FP64 maps
 cudaError_t launch_rhs(const hps_handle* h, const double2* s, const double2* t, double2* b, int nrhs,
-                       cudaStream_t st);
+                       cudaStream_t st, bool compensated = false);
+// Smallest solve tolerance at which the mixed form forms its restart residual and right-hand
+// side from the compensated FP32 maps (~3e-11 from the FP64 maps) instead of the FP64 maps.
+constexpr double kCompensatedMinTol = 1e-8;
 cudaError_t launch_precond(const hps_handle* h, bool fp32_matrix, VType tin, const void* r,
                            VType tout, void* z, void* scratch, int nrhs, cudaStream_t st, bool fp16_blocks = false);
 // Tensor-core apply for 64-RHS groups (tc_apply.cu); f complex float, y complex

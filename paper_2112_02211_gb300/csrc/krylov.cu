@@ -1088,8 +1088,11 @@ int gmres_solve(hps_handle* h, int form, const double2* b, double2* x, int nrhs,
   ops.precond = [h, mixed](VType tin, const void* in, VType tout, void* out, int nrhs, cudaStream_t s) {
     return launch_precond(h, mixed, tin, in, tout, out, h->ks.zt, nrhs, s, mixed && h->Kc16 != nullptr);
   };
-  ops.residual = [h](const double2* xx, const double2* bb, double2* r, int nrhs, cudaStream_t s) {
-    return timed_apply(h, HPS_PHASE_RESIDUAL, h->R64 == nullptr, VType::C128, xx, VType::C128, r, bb, nrhs, true, s);
+  // restart residual: FP64 maps, or the compensated FP32 maps (lean mode; the mixed form at
+  // tolerances >= 1e-8)
+  const bool cf_res = h->R64 == nullptr || (mixed && tol >= kCompensatedMinTol && compensated_maps(h));
+  ops.residual = [h, cf_res](const double2* xx, const double2* bb, double2* r, int nrhs, cudaStream_t s) {
+    return timed_apply(h, HPS_PHASE_RESIDUAL, cf_res, VType::C128, xx, VType::C128, r, bb, nrhs, true, s);
   };
   ops.c64_operand = mixed && apply_tc_eligible(h, nrhs);
   ops.id = 0;

@@ -51,8 +51,9 @@ def test_lean_covers_its_arrays(lib, L, p):
 
 @pytest.mark.parametrize("L,p", [(4, 8), (16, 10)])
 def test_both_forms_cover_their_arrays(lib, L, p):
-    # FP64 and FP32 maps, FP64 H, cluster inverses in FP64, FP32 and FP16
-    need = _arrays(L, p, r_bytes=16 + 8, h_bytes=16, k_bytes=16 + 8 + 4)
+    # FP64 and FP32 maps with the FP16 remainders of the FP32 ones (R and H), cluster inverses in
+    # FP64, FP32 and FP16
+    need = _arrays(L, p, r_bytes=16 + 8 + 4, h_bytes=16 + 8 + 4, k_bytes=16 + 8 + 4)
     got = _bytes(lib, L, p)
     assert need <= got <= 1.15 * need + 24 * GiB
 
