@@ -34,6 +34,7 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+T_START = time.time()
 sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
@@ -62,6 +63,9 @@ def parse():
     ap.add_argument("--configs", default="multi_rhs,large",
                     help="full-size configurations timed after the headline (comma list of multi_rhs, large; "
                          "'' = none)")
+    ap.add_argument("--budget-s", type=float, default=1500.0,
+                    help="wall-time budget of the whole run: a configuration leg that would end after it is "
+                         "skipped (with a note)")
     return ap.parse_args()
 
 
@@ -428,7 +432,14 @@ def run_gpu(args, dist):
     extra = [c for c in args.configs.split(",") if c]
     if extra:
         rec["configurations"] = {}
+        # measured wall time of each leg (setup dominates: FP64 elimination of every leaf)
+        expected_s = {"multi_rhs": 340.0, "large": 430.0}
         for name in extra:
+            elapsed = time.time() - T_START
+            if elapsed + expected_s.get(name, 300.0) > args.budget_s:
+                rec["configurations"][name] = {"skipped": f"would end after the {args.budget_s:.0f} s budget "
+                                                          f"({elapsed:.0f} s elapsed)"}
+                continue
             rec["configurations"][name] = run_config(name, dist)
     return rec
 
@@ -457,7 +468,7 @@ def run_config(name, dist):
     import paper_2112_02211_gb300 as hps
 
     if name == "multi_rhs":
-        w, nrhs, steps = W.multi_rhs_16cubed(), 64, 2
+        w, nrhs, steps = W.multi_rhs_16cubed(), 64, 1
     elif name == "large":
         w, nrhs, steps = W.large_32cubed(), 1, 3
     else:

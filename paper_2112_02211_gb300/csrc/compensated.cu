@@ -28,7 +28,9 @@ namespace {
 constexpr int kT = 256;
 constexpr int kW = kT / 32;
 constexpr int kRPW = 2;  // rows per warp pass
-constexpr int kNR = 4;   // right-hand sides per pass over the block
+constexpr int kNRMax = 4;  // most right-hand sides per pass over the block
+constexpr int kCR = 32;    // rows per work item: a face block is split so that the rows every
+                           // pass over the right-hand sides re-reads stay in L2
 
 // (sum, error) pair: value = s + c
 struct cacc {
@@ -66,21 +68,27 @@ struct CfArgs {
   long long nitems;
 };
 
+// kNR right-hand sides per pass over the block (1, 2 or 4)
+template <int kNR>
 __global__ void __launch_bounds__(kT) cf_gemv_kernel(const CfArgs A, int ncp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* xh = reinterpret_cast<float2*>(smraw);  // kNR x ncp
   float2* xl = xh + kNR * ncp;                    // kNR x ncp
-  double2* outs = reinterpret_cast<double2*>(xl + kNR * ncp);  // kNR x q2
+  double2* outs = reinterpret_cast<double2*>(xl + kNR * ncp);  // kNR x kCR
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q2 = A.q2;
+  const int nchunk = (q2 + kCR - 1) / kCR;
   for (long long item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int leaf = (int)(item / 6), face = (int)(item % 6);
+    const long long lf = item / nchunk;
+    const int chunk = (int)(item % nchunk);
+    const int leaf = (int)(lf / 6), face = (int)(lf % 6);
+    const int row0 = chunk * kCR, nrow = min(kCR, q2 - row0);
     const int nbr = A.g.neighbor(leaf, face);
     const long long own = (long long)leaf * A.nb + (long long)face * q2;
     if (nbr < 0) {
       // boundary face: R rows unused (Pi is 0 there); H: the slot takes t (or 0)
-      for (int idx = tid; idx < A.nrhs * q2; idx += kT) {
-        const int rr = idx / q2, j = idx % q2;
+      for (int idx = tid; idx < A.nrhs * nrow; idx += kT) {
+        const int rr = idx / nrow, j = row0 + idx % nrow;
         const long long o = (long long)rr * A.nf + own + j;
         if (A.rhs_mode) {
           A.y[o] = A.t ? A.t[o] : make_double2(0.0, 0.0);
@@ -93,13 +101,13 @@ __global__ void __launch_bounds__(kT) cf_gemv_kernel(const CfArgs A, int ncp) {
     }
     const long long dst = (long long)nbr * A.nb + (long long)(face ^ 1) * q2;
     if (A.rhs_mode && !A.x) {  // no body load: h = 0
-      for (int idx = tid; idx < A.nrhs * q2; idx += kT)
-        A.y[(long long)(idx / q2) * A.nf + dst + idx % q2] = make_double2(0.0, 0.0);
+      for (int idx = tid; idx < A.nrhs * nrow; idx += kT)
+        A.y[(long long)(idx / nrow) * A.nf + dst + row0 + idx % nrow] = make_double2(0.0, 0.0);
       continue;
     }
-    const float2* Mb = A.M + (long long)leaf * A.leaf_stride + (long long)face * q2 * A.ld;
-    const __half2* Lb = A.lo + (long long)leaf * A.leaf_stride + (long long)face * q2 * A.ld;
-    const float* Sb = A.scale + (long long)leaf * A.nb + (long long)face * q2;
+    const float2* Mb = A.M + (long long)leaf * A.leaf_stride + (long long)(face * q2 + row0) * A.ld;
+    const __half2* Lb = A.lo + (long long)leaf * A.leaf_stride + (long long)(face * q2 + row0) * A.ld;
+    const float* Sb = A.scale + (long long)leaf * A.nb + (long long)face * q2 + row0;
     for (int r0 = 0; r0 < A.nrhs; r0 += kNR) {
       const int nr = min(kNR, A.nrhs - r0);
       __syncthreads();
@@ -112,13 +120,13 @@ __global__ void __launch_bounds__(kT) cf_gemv_kernel(const CfArgs A, int ncp) {
         xl[idx] = make_float2(__double2float_rn(v.x - (double)hr), __double2float_rn(v.y - (double)hi));
       }
       __syncthreads();
-      for (int rw = warp * kRPW; rw < q2; rw += kW * kRPW) {
+      for (int rw = warp * kRPW; rw < nrow; rw += kW * kRPW) {
         cacc are[kRPW][kNR], aim[kRPW][kNR];
         float sre[kRPW][kNR], sim[kRPW][kNR];
         float sig[kRPW];
 #pragma unroll
         for (int i = 0; i < kRPW; ++i) {
-          sig[i] = (rw + i < q2) ? Sb[rw + i] : 0.f;
+          sig[i] = (rw + i < nrow) ? Sb[rw + i] : 0.f;
 #pragma unroll
           for (int rr = 0; rr < kNR; ++rr) {
             are[i][rr] = {0.f, 0.f};
@@ -130,7 +138,7 @@ __global__ void __launch_bounds__(kT) cf_gemv_kernel(const CfArgs A, int ncp) {
         for (int c = lane * 2; c < ncp; c += 64) {
 #pragma unroll
           for (int i = 0; i < kRPW; ++i) {
-            if (rw + i >= q2) continue;
+            if (rw + i >= nrow) continue;
             const float4 m = __ldg(reinterpret_cast<const float4*>(Mb + (long long)(rw + i) * A.ld + c));
             const uint2 lraw = __ldg(reinterpret_cast<const uint2*>(Lb + (long long)(rw + i) * A.ld + c));
             const float2 l0 = __half22float2(*reinterpret_cast<const __half2*>(&lraw.x));
@@ -176,19 +184,19 @@ __global__ void __launch_bounds__(kT) cf_gemv_kernel(const CfArgs A, int ncp) {
         if (lane == 0) {
 #pragma unroll
           for (int i = 0; i < kRPW; ++i)
-            if (rw + i < q2)
+            if (rw + i < nrow)
 #pragma unroll
               for (int rr = 0; rr < kNR; ++rr)
-                outs[rr * q2 + rw + i] =
+                outs[rr * kCR + rw + i] =
                     make_double2((double)are[i][rr].s + (double)are[i][rr].c + (double)sre[i][rr],
                                  (double)aim[i][rr].s + (double)aim[i][rr].c + (double)sim[i][rr]);
         }
       }
       __syncthreads();
-      for (int idx = tid; idx < nr * q2; idx += kT) {
-        const int rr = idx / q2, j = idx % q2;
+      for (int idx = tid; idx < nr * nrow; idx += kT) {
+        const int rr = idx / nrow, jj = idx % nrow, j = row0 + jj;
         const long long o = (long long)(r0 + rr) * A.nf + dst + j;
-        const double2 gv = outs[rr * q2 + j];
+        const double2 gv = outs[rr * kCR + jj];
         if (A.rhs_mode) {
           A.y[o] = make_double2(-gv.x, -gv.y);
         } else {
@@ -227,6 +235,28 @@ __global__ void split_lo_kernel(const double2* M, long long rows, int ld, __half
   }
 }
 
+template <int kNR>
+cudaError_t launch_cf_nr(const hps_handle* h, const CfArgs& A, int ncp, cudaStream_t st) {
+  const size_t smem = (size_t)2 * kNR * ncp * sizeof(float2) + (size_t)kNR * kCR * sizeof(double2);
+  auto kern = cf_gemv_kernel<kNR>;
+  cudaError_t e = allow_dynamic_smem((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kT, smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = std::min<long long>(A.nitems, (long long)h->nsm * std::max(occ, 1));
+  kern<<<(unsigned)grid, kT, smem, st>>>(A, ncp);
+  ++h->prof.launches;
+  return cudaGetLastError();
+}
+
+// one pass per group of up to 4 right-hand sides (a single right-hand side computes one)
+cudaError_t launch_cf(const hps_handle* h, const CfArgs& A, int ncp, cudaStream_t st) {
+  if (A.nrhs == 1) return launch_cf_nr<1>(h, A, ncp, st);
+  if (A.nrhs == 2) return launch_cf_nr<2>(h, A, ncp, st);
+  return launch_cf_nr<kNRMax>(h, A, ncp, st);
+}
+
 }  // namespace
 
 cudaError_t launch_split_lo(const double2* M, long long rows, int ld, __half2* lo, float* scale, cudaStream_t st) {
@@ -262,18 +292,8 @@ cudaError_t launch_apply_cf(const hps_handle* h, const double2* x, double2* y, c
   A.nf = h->nf;
   A.nrhs = nrhs;
   A.rhs_mode = 0;
-  A.nitems = (long long)h->nl * 6;
-  const int ncp = (int)round_up(h->ldR, 2);
-  const size_t smem = (size_t)2 * kNR * ncp * sizeof(float2) + (size_t)kNR * A.q2 * sizeof(double2);
-  cudaError_t e = allow_dynamic_smem((const void*)cf_gemv_kernel, smem);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cf_gemv_kernel, kT, smem);
-  if (e != cudaSuccess) return e;
-  const long long grid = std::min<long long>(A.nitems, (long long)h->nsm * std::max(occ, 1));
-  cf_gemv_kernel<<<(unsigned)grid, kT, smem, st>>>(A, ncp);
-  ++h->prof.launches;
-  return cudaGetLastError();
+  A.nitems = (long long)h->nl * 6 * ((A.q2 + kCR - 1) / kCR);
+  return launch_cf(h, A, (int)round_up(h->ldR, 2), st);
 }
 
 // b = tbar - Pi (H s) with the compensated FP32 maps H; s: [nrhs][nint] or nullptr.
@@ -299,18 +319,8 @@ cudaError_t launch_rhs_cf(const hps_handle* h, const double2* s, const double2* 
   A.nf = h->nf;
   A.nrhs = nrhs;
   A.rhs_mode = 1;
-  A.nitems = (long long)h->nl * 6;
-  const int ncp = (int)round_up(h->ldH, 2);
-  const size_t smem = (size_t)2 * kNR * ncp * sizeof(float2) + (size_t)kNR * A.q2 * sizeof(double2);
-  cudaError_t e = allow_dynamic_smem((const void*)cf_gemv_kernel, smem);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cf_gemv_kernel, kT, smem);
-  if (e != cudaSuccess) return e;
-  const long long grid = std::min<long long>(A.nitems, (long long)h->nsm * std::max(occ, 1));
-  cf_gemv_kernel<<<(unsigned)grid, kT, smem, st>>>(A, ncp);
-  ++h->prof.launches;
-  return cudaGetLastError();
+  A.nitems = (long long)h->nl * 6 * ((A.q2 + kCR - 1) / kCR);
+  return launch_cf(h, A, (int)round_up(h->ldR, 2), st);
 }
 
 }  // namespace hps

@@ -68,6 +68,54 @@ def accuracy_case(kind="plane", L=4, p=16, ppw=24.0, tol=1e-13):
             "rel_residual": info1["rel_residual"], "rel_residual_rprr": info2["rel_residual"]}
 
 
+def accuracy_table(L=4, p=16, ppws=(24.0, 16.0, 9.6), tol=1e-13):
+    """Tables PlaneMinErr / PlaneResRed and BumpsMinErr2 (Sec. 6.2-6.3) on L^3 leaves: per points
+    per wavelength one setup (both exact solutions live in the same bump medium at the same
+    kappa, so they share the leaf maps), then for each solution the FP64 solve to `tol` (E_h)
+    and to the table's residual reduction (E_h^it), as in accuracy_case."""
+    import time
+
+    import torch
+
+    import workloads as W
+
+    from . import Solver, face_normals, nodes
+    xi, xf, xc = nodes(L, L, L, p, cheb_faces=True)
+    nrm = np.broadcast_to(face_normals()[None, :, None, :], xf.shape)
+    rows = []
+    for ppw in ppws:
+        kappa = 2.0 * math.pi * 12.0 * L / ppw
+        rprr = RPRR.get(ppw, 1e-10)
+        wp = W.manufactured(L=L, p=p, kappa=kappa)
+        t0 = time.time()
+        solver = Solver(L, L, L, p, kappa=kappa, eta=kappa, b=wp.sample_b(xi), forms=("fp64",), cluster=0,
+                        max_rhs=2)
+        setup_s = time.time() - t0
+        try:
+            for kind, make in (("plane", W.manufactured), ("bumps", W.manufactured_bumps)):
+                w = make(L=L, p=p, kappa=kappa)
+                s = torch.from_numpy(w.sample_s(xi).reshape(-1)).cuda()
+                t = torch.from_numpy(w.sample_t(xf, nrm).reshape(-1)).cuda()
+                f1, info1 = solver.solve(s=s, t=t, tol=tol, form="fp64")
+                f2, info2 = solver.solve(s=s, t=t, tol=rprr, form="fp64")
+                u, uf = solver.recover(torch.cat([f1, f2]), s=torch.cat([s, s]), nrhs=2, faces=True)
+                u, uf = u.cpu().numpy().reshape(2, -1), uf.cpu().numpy().reshape(2, -1)
+                ue, ufe = w.meta["u"](xi).reshape(-1), w.meta["u"](xc).reshape(-1)
+                den = np.linalg.norm(ue) ** 2 + np.linalg.norm(ufe) ** 2
+
+                def e_h(r):
+                    return float(np.sqrt((np.linalg.norm(u[r] - ue) ** 2 + np.linalg.norm(uf[r] - ufe) ** 2) / den))
+
+                rows.append({"kind": kind, "leaves": L, "p": p, "ppw": ppw, "kappa": kappa, "E_h": e_h(0),
+                             "E_h_it": e_h(1), "rprr": rprr, "iterations": info1["iterations"],
+                             "iterations_rprr": info2["iterations"], "rel_residual": info1["rel_residual"],
+                             "setup_s": setup_s})
+                print(json.dumps(rows[-1]), flush=True)
+        finally:
+            solver.close()
+    return rows
+
+
 def plane_min_err(L=4, p=16, ppw=24.0, tol=1e-13):
     """Table PlaneMinErr entry (see accuracy_case)."""
     return accuracy_case("plane", L=L, p=p, ppw=ppw, tol=tol)
@@ -229,7 +277,12 @@ def main():
     ap.add_argument("--large", action="store_true", help="run the 32^3-leaf large solve instead")
     ap.add_argument("--multi-rhs", action="store_true", help="run the 64-RHS tensor-core workload instead")
     ap.add_argument("--sharing", action="store_true", help="run the shared-preconditioner-block sweep instead")
+    ap.add_argument("--table", action="store_true",
+                    help="both accuracy tables, one setup per points-per-wavelength value")
     args = ap.parse_args()
+    if args.table:
+        accuracy_table(L=args.L, ppws=tuple(args.ppw))
+        return
     if args.sharing:
         for row in precond_sharing(L=args.L if args.L != 4 else 16):
             print(json.dumps(row), flush=True)
