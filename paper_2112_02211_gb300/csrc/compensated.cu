@@ -320,7 +320,7 @@ cudaError_t launch_rhs_cf(const hps_handle* h, const double2* s, const double2* 
   A.nrhs = nrhs;
   A.rhs_mode = 1;
   A.nitems = (long long)h->nl * 6 * ((A.q2 + kCR - 1) / kCR);
-  return launch_cf(h, A, (int)round_up(h->ldR, 2), st);
+  return launch_cf(h, A, (int)round_up(h->ldH, 2), st);
 }
 
 }  // namespace hps
