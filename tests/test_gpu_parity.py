@@ -177,6 +177,31 @@ def test_lean_mode_solve(ragged):
         solver.close()
 
 
+@pytest.mark.parametrize("p", [7, 10, 12])
+def test_compensated_maps_match_the_fp64_maps(p):
+    """The compensated FP32 maps (FP32 rounding + FP16 remainder per row) against the FP64 maps
+    of a handle built from the same medium: right-hand sides with 1 and 3 sources and
+    complex-double applies with 1, 2 and 5 right-hand sides, at 1e-9.  p = 7, 10, 12 make the
+    body-load map H narrower than, wider than and much wider than the ItI map (n1^3 vs 6q^2)."""
+    w = W.manufactured(L=1, p=p, kappa=9.0)
+    w.nx, w.ny, w.nz = 2, 2, 1
+    xi, xf, b, s, t = gpu_inputs(w, hps)
+    full = hps.Solver(2, 2, 1, p, kappa=9.0, eta=w.eta, b=b, cluster=0, max_rhs=5)
+    lean = hps.Solver(2, 2, 1, p, kappa=9.0, eta=w.eta, b=b, forms=("mixed",), lean=True, cluster=0, max_rhs=5)
+    try:
+        rng = np.random.default_rng(p)
+        for nrhs in (1, 3):
+            sv = torch.from_numpy(rng.standard_normal(nrhs * full.nl * full.ni) + 0.5j).cuda()
+            tv = torch.from_numpy(rng.standard_normal(nrhs * full.nf) + 1j).cuda()
+            assert rel(lean.rhs(sv, tv, nrhs=nrhs).cpu().numpy(), full.rhs(sv, tv, nrhs=nrhs).cpu().numpy()) < 1e-9
+        for nrhs in (1, 2, 5):
+            f = torch.from_numpy(_rand(full.nf, 60 + nrhs, nrhs).reshape(-1)).cuda()
+            assert rel(lean.apply(f).cpu().numpy(), full.apply(f).cpu().numpy()) < 1e-9, nrhs
+    finally:
+        full.close()
+        lean.close()
+
+
 def test_rhs_matches_oracle(ragged):
     w, oc, solver, (xi, xf, b, s, t) = ragged
     bg = solver.rhs(torch.from_numpy(s.reshape(-1)).cuda(), torch.from_numpy(t.reshape(-1)).cuda())
