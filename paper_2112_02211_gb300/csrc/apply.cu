@@ -412,21 +412,12 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
         Acc acc[NR];
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) acc[rr] = czero<Acc>();
-        // kBU independent loads in flight per thread before their FMAs (the loads are L2 hits for
-        // shared blocks; latency, not bandwidth, bounds this kernel)
-        constexpr int kBU = 16;
-        for (int c0 = 0; c0 < ncols; c0 += kBU) {
-          Acc bv[kBU];
+#pragma unroll 4
+        for (int c = 0; c < ncols; ++c) {
+          const Acc bv = load_one<TM>(Bm + (long long)c * ldr + row);
 #pragma unroll
-          for (int u = 0; u < kBU; ++u)
-            bv[u] = (c0 + u < ncols) ? load_one<TM>(Bm + (long long)(c0 + u) * ldr + row) : czero<Acc>();
-#pragma unroll
-          for (int u = 0; u < kBU; ++u) {
-            if (c0 + u >= ncols) break;
-#pragma unroll
-            for (int rr = 0; rr < NR; ++rr)
-              if (rr < nr) cfma(acc[rr], bv[u], xs[rr * ncols + c0 + u]);
-          }
+          for (int rr = 0; rr < NR; ++rr)
+            if (rr < nr) cfma(acc[rr], bv, xs[rr * ncols + c]);
         }
         const int k = row / q2, j = row - k * q2;
         const int e = leaf * 6 + k;
