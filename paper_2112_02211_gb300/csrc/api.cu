@@ -116,7 +116,7 @@ void free_handle(hps_handle* h) {
                   h->dct.int_mask, h->dct.b_off, h->dct.leaf_bcls, h->dct.bc_rep, h->dct.kc_off,
                   h->dct.kc_slot_begin, h->dct.kslot_class, h->dct.kc_members, h->dct.kitems[0], h->dct.kitems[1],
                   h->dct.kitems[2], h->dct.kitems[3], h->dct.cl_tpos, h->dct.lf_tpos, h->dct.brd, h->dct.bto,
-                  h->dct.bsc, h->dct.pos_class, h->fs.d_cls, h->fs.Sinv64, h->fs.Sinv32, h->fs.eig};
+                  h->dct.bsc, h->dct.pos_class, h->dct.leaf_cluster, h->dct.tc16_items, h->tmax, h->fs.d_cls, h->fs.Sinv64, h->fs.Sinv32, h->fs.eig};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -345,6 +345,10 @@ int hps_setup(const hps_grid* g, double kappa, double eta, const double* b, cons
       }
       const size_t ts = (size_t)ct.tsize * o.max_rhs * sizeof(double2);
       if ((r = dalloc(h, &h->pc_scratch, ts))) return r;
+      if (fp16) {  // per-cluster scales of t for the FP16 tensor-core stage K
+        if ((r = dalloc(h, (void**)&h->tmax, (size_t)ct.ncl * o.max_rhs * sizeof(float)))) return r;
+        h->tmax_rhs = o.max_rhs;
+      }
       if ((r = build_preconditioner(h, dc, st))) return r;
       if (fp16 && (r = build_precond_fp16(h, st))) return r;
     }
@@ -403,7 +407,8 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
                            // the multi-RHS tensor-core stage K
       bytes += (o.tc_apply && ct.uniform && o.max_rhs >= 64) ? (size_t)ct.kc_elems * c8
                                                               : std::min<size_t>((size_t)ct.kc_elems * c8, (size_t)4 << 30);
-    bytes += (size_t)ct.ncl * sizeof(int);  // stage-K position -> block
+    bytes += (size_t)ct.ncl * sizeof(int) + (size_t)h.nl * sizeof(int) +      // position -> block, leaf -> cluster
+             (size_t)ct.ncl * o.max_rhs * sizeof(float) + ct.tc16_items.size() * sizeof(int4);  // t scales, items
     if (want32 && (o.precond_fp16 || o.lean))
       bytes += (size_t)(ct.kc_elems + ct.b_elems) * sizeof(__half2) + nslots * q2 * sizeof(float) +
                (size_t)h.nl * 6 * q2 * sizeof(float);

@@ -31,6 +31,13 @@
 
 namespace hps {
 
+// Returns the CUDA error of expr from a function that returns cudaError_t.
+#define HPS_TRY_CUDA_E(expr)          \
+  do {                                \
+    const cudaError_t e_ = (expr);    \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -376,6 +383,12 @@ struct PrecBArgs {
   int nrhs;
   long long vstride, tstride;  // per right-hand side: r and z, t
   const int* gate;  // as in seg_gemv_kernel
+  // optional: the largest |component| of t per (right-hand side, cluster), as float bits
+  // (non-negative floats order like their bit patterns, so atomicMax gives the same result in
+  // any order); the scale of the FP16 tensor-core stage K
+  unsigned* tmax;
+  const int* leaf_cluster;
+  int ncl;
 };
 
 template <class TM> __device__ __forceinline__ typename MT<TM>::Acc load_one(const TM* p);
@@ -408,6 +421,9 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
       }
       __syncthreads();
       if (nint == 0) continue;
+      float tmx[NR];
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr) tmx[rr] = 0.f;
       for (int row = threadIdx.x; row < nrows; row += kThreads) {
         Acc acc[NR];
 #pragma unroll
@@ -426,7 +442,22 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
           if (rr >= nr) break;
           const Acc g = rscale(acc[rr], A.bscale, (long long)A.bsc[e] + j);
           const Acc v = csub(cvt<Acc>(A.r[(long long)(r0 + rr) * A.vstride + A.brd[e] + j]), g);
-          A.t[(long long)(r0 + rr) * A.tstride + A.bto[e] + j] = cvt<TOUT>(v);
+          const TOUT tv = cvt<TOUT>(v);
+          A.t[(long long)(r0 + rr) * A.tstride + A.bto[e] + j] = tv;
+          if constexpr (std::is_same<TOUT, float2>::value) tmx[rr] = fmaxf(tmx[rr], fmaxf(fabsf(tv.x), fabsf(tv.y)));
+        }
+      }
+      if constexpr (std::is_same<TOUT, float2>::value) {
+        if (A.tmax) {
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) {
+            float m = tmx[rr];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0 && rr < nr && m > 0.f)
+              atomicMax(A.tmax + (long long)(r0 + rr) * A.ncl + A.leaf_cluster[leaf], __float_as_uint(m));
+            tmx[rr] = 0.f;
+          }
         }
       }
     }
@@ -537,6 +568,11 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
                       bool use_tc = false) {
   const int q2 = h->q * h->q;
   const long long tstride = h->ct.tsize;
+  // FP16 blocks with complex-float output on the uniform layout: stage K of every block on the
+  // tensor cores with FP16 operands, t scaled per cluster (stage B records the scales)
+  bool tc16 = false;
+  if constexpr (std::is_same<TM, __half2>::value && std::is_same<TOUT, float2>::value)
+    tc16 = precond_tc16_eligible(h, nrhs);
   {
     PrecBArgs<TM, TIN, TOUT> A;
     A.B = B;
@@ -555,6 +591,13 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.nrhs = nrhs;
     A.vstride = h->nf;
     A.tstride = tstride;
+    A.tmax = nullptr;
+    A.leaf_cluster = h->dct.leaf_cluster;
+    A.ncl = h->ct.ncl;
+    if (tc16) {
+      HPS_TRY_CUDA_E(cudaMemsetAsync(h->tmax, 0, (size_t)h->ct.ncl * nrhs * sizeof(float), st));
+      A.tmax = reinterpret_cast<unsigned*>(h->tmax);
+    }
     using Acc = typename MT<TM>::Acc;
     cudaEvent_t ev = h->prof.begin(st);
     auto launch_b = [&](auto kern, int nr) -> cudaError_t {
@@ -579,6 +622,12 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     if (e != cudaSuccess) return e;
   }
   if (h->ct.nslots == 0) return cudaSuccess;
+  if (tc16) {
+    cudaEvent_t ev = h->prof.begin(st);
+    const cudaError_t e = launch_precond_tc16(h, (const float2*)t, (float2*)z, nrhs, st);
+    h->prof.end(HPS_PHASE_PRECOND_K, ev, st);
+    return e;
+  }
   if constexpr (std::is_same<TOUT, float2>::value) {
     // many right-hand sides: every block once per 64 of them, on the tensor cores
     if (precond_tc_multi_eligible(h, nrhs)) {

@@ -115,7 +115,12 @@ struct ClusterTables {
   // blocks form one 3D array and t one [position][nint] matrix per right-hand
   // side, so the multi-RHS tensor-core stage K runs every block in one launch.
   bool uniform = false;
+  int nint0 = 0;                     // internal values of every cluster when uniform
   std::vector<int> pos_class;        // [ncl] K block of the member at stage-K position m
+  std::vector<int> leaf_cluster;     // [nleaves] cluster of each leaf
+  // FP16 tensor-core stage K of one right-hand side (uniform layout): items (block, 128-row
+  // tile, first member position, members <= 64)
+  std::vector<int4> tc16_items;
 };
 
 struct DeviceClusterTables {
@@ -139,6 +144,8 @@ struct DeviceClusterTables {
   int* bto = nullptr;
   int* bsc = nullptr;
   int* pos_class = nullptr;
+  int* leaf_cluster = nullptr;
+  int4* tc16_items = nullptr;
 };
 
 // Launch shape of the batched GEMV kernels: matrix rows per warp pass and a cap on
@@ -360,6 +367,8 @@ struct hps_handle {
   __half2* B16 = nullptr;   // FP16 copies of B, rows scaled by 1/B16s[(bcls*6+face)*q^2 + j]
   float* B16s = nullptr;
   void* pc_scratch = nullptr;  // nslots*q^2*max_rhs complex double (precond t buffer)
+  float* tmax = nullptr;       // [rhs][cluster] largest |component| of stage B's t (FP16 stage K scale)
+  int tmax_rhs = 0;            // right-hand sides tmax holds
 
   int* tc_error = nullptr;  // device error word of the tensor-core kernels
   // While a GMRES cycle is captured: the device word that the per-step kernels
@@ -445,6 +454,11 @@ cudaError_t launch_precond_tc(const hps_handle* h, const float2* t, float2* z, i
 // in one launch (complex-FP32 blocks, one TF32 product): the GEMM of each K_c against the
 // columns (member cluster, right-hand side).  Needs ct.uniform.  t: [rhs][tsize], z: [rhs][nf].
 bool precond_tc_multi_eligible(const hps_handle* h, int nrhs);
+// Stage K of every cluster block on the tensor cores with FP16 operands (tc_precond16.cu): the
+// FP16 blocks against t scaled per cluster by tmax (which stage B fills); one right-hand side or
+// 64, 128, ... of them; needs the uniform layout.
+bool precond_tc16_eligible(const hps_handle* h, int nrhs);
+cudaError_t launch_precond_tc16(const hps_handle* h, const float2* t, float2* z, int nrhs, cudaStream_t st);
 cudaError_t launch_precond_tc_multi(const hps_handle* h, const float2* t, float2* z, int nrhs, int* d_error,
                                     cudaStream_t st);
 // Timed wrappers (phase intervals recorded when profiling is on).

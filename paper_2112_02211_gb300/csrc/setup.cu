@@ -952,6 +952,9 @@ void build_cluster_tables(hps_handle* h, int width) {
       }
   ct.max_ext = 0;
   for (int leaf = 0; leaf < h->nl; ++leaf) ct.max_ext = std::max(ct.max_ext, 6 - __builtin_popcount(ct.int_mask[leaf]));
+  ct.leaf_cluster.assign(h->nl, 0);
+  for (int c = 0; c < ct.ncl; ++c)
+    for (int l = ct.cl_leaf_begin[c]; l < ct.cl_leaf_begin[c + 1]; ++l) ct.leaf_cluster[ct.cl_leaves[l]] = c;
   assign_blocks(h, nullptr);
 }
 
@@ -1118,6 +1121,17 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
         ct.uniform = false;
     for (int m = 0; m < ct.ncl && ct.uniform; ++m)
       if (ct.cl_tpos[ct.kc_members[m]] != m * nint0) ct.uniform = false;
+    ct.nint0 = ct.uniform ? (int)nint0 : 0;
+  }
+  // FP16 tensor-core stage K items of one right-hand side: per block, per 128-row tile, the
+  // members in tiles of 64 (consecutive items reuse the block's row tile from L2)
+  ct.tc16_items.clear();
+  if (ct.uniform && ct.nint0 % 32 == 0) {
+    const int mtiles = (ct.nint0 + 127) / 128;
+    for (int k = 0; k < ct.nkc; ++k)
+      for (int mt = 0; mt < mtiles; ++mt)
+        for (int p0 = ct.kc_mem_begin[k]; p0 < ct.kc_mem_begin[k + 1]; p0 += 64)
+          ct.tc16_items.push_back(make_int4(k, mt, p0, std::min(64, ct.kc_mem_begin[k + 1] - p0)));
   }
   // blocks for the tensor-core path: many members, an even row length (16-byte
   // aligned member rows of complex floats)
@@ -1314,6 +1328,8 @@ int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st
   if ((rc = upload(h, h->dct.bto, ct.bto, st))) return rc;
   if ((rc = upload(h, h->dct.bsc, ct.bsc, st))) return rc;
   if ((rc = upload(h, h->dct.pos_class, ct.pos_class, st))) return rc;
+  if ((rc = upload(h, h->dct.leaf_cluster, ct.leaf_cluster, st))) return rc;
+  if ((rc = upload(h, h->dct.tc16_items, ct.tc16_items, st))) return rc;
   for (int i = 0; i < 4; ++i)
     if ((rc = upload(h, h->dct.kitems[i], ct.kitems[i], st))) return rc;
   HPS_CUDA_TRY(cudaStreamSynchronize(st));
