@@ -8,9 +8,11 @@ s = exp(-400 |x - x0|^2), t = 0, relative tolerance 1e-6.
 
 A step is one solve to tolerance through the C ABI: RHS build, restarted
 GMRES(50) with the leaf ItI apply + face swap, the cluster block-Jacobi
-preconditioner, CGS2 Arnoldi and FP64 restart residuals.  `value` is face
-unknowns solved per second with the inputs already in HBM (mixed form:
-complex-FP32 operators inside FP64 Krylov + FP64 restart residual); the FP64
+preconditioner, classical Gram-Schmidt Arnoldi (a second pass where
+Rutishauser's test asks for it) and FP64-accurate restart residuals.  `value`
+is face unknowns solved per second with the inputs already in HBM (mixed form:
+complex-FP32 operators, double-float Krylov basis, restart residual from the
+FP32 maps plus their FP16 remainders at tol >= 1e-8, else FP64); the FP64
 form and the runs without preconditioner are reported beside it.  Setup
 (leaf maps, preconditioner) is outside the timed region.
 
@@ -255,6 +257,7 @@ def run_gpu(args, dist):
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     ncl, k_blocks, b_blocks = solver.precond_info()
+    shapes = solver.launch_shapes()
     nf = solver.nf
     s_dev = torch.from_numpy(s).cuda()
     out = torch.empty(nf, dtype=torch.complex128, device="cuda")
@@ -363,10 +366,13 @@ def run_gpu(args, dist):
     # double-float (16-byte) input to stage B
     kb, bb = precond_bytes(L, q, 4, 8, in_bytes=16, scale_bytes=4, k_blocks=k_blocks, b_blocks=b_blocks)
     phases = {"apply": a_bytes, "precond_k": kb, "precond_b": bb}
-    kernels = {"apply": "seg_gemv_kernel<ApplyP<float2,float2,float4>,1,4>",
-               "precond_k": "tc_precond_kernel (blocks shared by >= 16 clusters) + "
-                            "seg_gemv_kernel<PrecKP<__half2,float2,float2>,W,R> (W = 1, 2, 4, 8 clusters per block)",
-               "precond_b": "prec_b_kernel<__half2,float4,float2> (one thread per row, B transposed)"}
+    rpw = shapes["apply_rows_per_warp"][0][0]
+    kernels = {"apply": f"seg_gemv_kernel<ApplyP<float2,float2,float4>,1,{rpw}> (rows per warp chosen at setup)",
+               "precond_k": "tc_precond16_kernel<false> (every cluster block on the tensor cores, kind::f16, "
+                            "t scaled per cluster) when the clusters are uniform, else "
+                            "seg_gemv_kernel<PrecKP<__half2,float2,float2>,1,R>",
+               "precond_b": "prec_b_kernel<__half2,float4,float2,8> (8 leaves sharing a B block per item, "
+                            "one thread per row)"}
     roof = {}
     for ph, by in phases.items():
         cnt = prof["count"][ph]
@@ -400,8 +406,10 @@ def run_gpu(args, dist):
         "data": "synthetic",
         "config": {
             "workload": workload_name(w),
-            "form": "mixed (complex-FP32 apply and preconditioner, CGS2 Arnoldi in double-float "
-                    "(FP64-accurate, FP32 pipe), FP64 restart residual)",
+            "form": "mixed (complex-FP32 apply and preconditioner, classical Gram-Schmidt Arnoldi in "
+                    "double-float with a second pass on Rutishauser's test, restart residual from the "
+                    "FP32 maps plus FP16 remainders (FP64-level))",
+            "launch_shapes": shapes,
             "preconditioner": "2x2x2 cluster block Jacobi, homogenized leaf maps, blocks in FP16 with FP32 row scales",
             "lambda_bin": args.lambda_bin,
             "precond_blocks": {"clusters": ncl, "distinct_K": k_blocks, "distinct_B": b_blocks},

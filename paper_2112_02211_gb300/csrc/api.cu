@@ -116,7 +116,7 @@ void free_handle(hps_handle* h) {
                   h->dct.int_mask, h->dct.b_off, h->dct.leaf_bcls, h->dct.bc_rep, h->dct.kc_off,
                   h->dct.kc_slot_begin, h->dct.kslot_class, h->dct.kc_members, h->dct.kitems[0], h->dct.kitems[1],
                   h->dct.kitems[2], h->dct.kitems[3], h->dct.cl_tpos, h->dct.lf_tpos, h->dct.brd, h->dct.bto,
-                  h->dct.bsc, h->dct.pos_class, h->dct.leaf_cluster, h->dct.tc16_items, h->tmax, h->fs.d_cls, h->fs.Sinv64, h->fs.Sinv32, h->fs.eig};
+                  h->dct.bsc, h->dct.pos_class, h->dct.leaf_cluster, h->dct.tc16_items, h->dct.bgroup_leaves, h->dct.bgroups, h->tmax, h->fs.d_cls, h->fs.Sinv64, h->fs.Sinv32, h->fs.eig};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -408,7 +408,8 @@ size_t hps_setup_bytes(const hps_grid* g, const hps_options* opt, int nrhs) {
       bytes += (o.tc_apply && ct.uniform && o.max_rhs >= 64) ? (size_t)ct.kc_elems * c8
                                                               : std::min<size_t>((size_t)ct.kc_elems * c8, (size_t)4 << 30);
     bytes += (size_t)ct.ncl * sizeof(int) + (size_t)h.nl * sizeof(int) +      // position -> block, leaf -> cluster
-             (size_t)ct.ncl * o.max_rhs * sizeof(float) + ct.tc16_items.size() * sizeof(int4);  // t scales, items
+             (size_t)ct.ncl * o.max_rhs * sizeof(float) + ct.tc16_items.size() * sizeof(int4) +  // t scales, items
+             (size_t)h.nl * (sizeof(int) + sizeof(int2));  // stage-B groups
     if (want32 && (o.precond_fp16 || o.lean))
       bytes += (size_t)(ct.kc_elems + ct.b_elems) * sizeof(__half2) + nslots * q2 * sizeof(float) +
                (size_t)h.nl * 6 * q2 * sizeof(float);

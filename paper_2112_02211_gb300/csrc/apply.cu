@@ -389,6 +389,10 @@ struct PrecBArgs {
   unsigned* tmax;
   const int* leaf_cluster;
   int ncl;
+  // work items: groups of leaves sharing one B block, as (first index into gleaves, count)
+  const int2* groups;
+  const int* gleaves;
+  int ngroups;
 };
 
 template <class TM> __device__ __forceinline__ typename MT<TM>::Acc load_one(const TM* p);
@@ -401,20 +405,27 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
   if (A.gate && *A.gate == 0) return;
   using Acc = typename MT<TM>::Acc;
   extern __shared__ __align__(16) unsigned char smraw[];
-  Acc* xs = reinterpret_cast<Acc*>(smraw);  // NR x 3 q^2 (external columns)
+  Acc* xs = reinterpret_cast<Acc*>(smraw);  // NR x (external columns)
   const int q2 = A.q2;
-  for (int leaf = blockIdx.x; leaf < A.nl; leaf += gridDim.x) {
-    const int nint = __popc((unsigned)A.int_mask[leaf]);
+  // item: a group of leaves sharing one B block (same block, same internal-face mask); the
+  // vectors of a pass are NR (leaf of the group, right-hand side) pairs, so every entry of B
+  // loaded from L2 serves NR independent accumulations
+  for (int item = blockIdx.x; item < A.ngroups; item += gridDim.x) {
+    const int2 grp = A.groups[item];
+    const int leaf0 = A.gleaves[grp.x];
+    const int nint = __popc((unsigned)A.int_mask[leaf0]);
     const int ncols = (6 - nint) * q2, nrows = nint * q2;
-    const TM* Bm = A.B + A.b_off[leaf];
+    const TM* Bm = A.B + A.b_off[leaf0];
     const int ldr = (int)rup4(nrows);
-    for (int r0 = 0; r0 < A.nrhs; r0 += NR) {
-      const int nr = min(NR, A.nrhs - r0);
+    const int nvec = grp.y * A.nrhs;
+    for (int v0 = 0; v0 < nvec; v0 += NR) {
+      const int nr = min(NR, nvec - v0);
       __syncthreads();
       for (int idx = threadIdx.x; idx < nr * ncols; idx += kThreads) {
         const int rr = idx / ncols, c = idx - rr * ncols;
+        const int vid = v0 + rr, leaf = A.gleaves[grp.x + vid / A.nrhs], rhs = vid % A.nrhs;
         const int k = c / q2;
-        const long long o = (long long)(r0 + rr) * A.vstride + A.brd[leaf * 6 + nint + k] + (c - k * q2);
+        const long long o = (long long)rhs * A.vstride + A.brd[leaf * 6 + nint + k] + (c - k * q2);
         const Acc v = cvt<Acc>(A.r[o]);
         xs[rr * ncols + c] = v;
         A.z[o] = cvt<TOUT>(v);
@@ -436,14 +447,15 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
             if (rr < nr) cfma(acc[rr], bv, xs[rr * ncols + c]);
         }
         const int k = row / q2, j = row - k * q2;
-        const int e = leaf * 6 + k;
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) {
           if (rr >= nr) break;
+          const int vid = v0 + rr, leaf = A.gleaves[grp.x + vid / A.nrhs], rhs = vid % A.nrhs;
+          const int e = leaf * 6 + k;
           const Acc g = rscale(acc[rr], A.bscale, (long long)A.bsc[e] + j);
-          const Acc v = csub(cvt<Acc>(A.r[(long long)(r0 + rr) * A.vstride + A.brd[e] + j]), g);
+          const Acc v = csub(cvt<Acc>(A.r[(long long)rhs * A.vstride + A.brd[e] + j]), g);
           const TOUT tv = cvt<TOUT>(v);
-          A.t[(long long)(r0 + rr) * A.tstride + A.bto[e] + j] = tv;
+          A.t[(long long)rhs * A.tstride + A.bto[e] + j] = tv;
           if constexpr (std::is_same<TOUT, float2>::value) tmx[rr] = fmaxf(tmx[rr], fmaxf(fabsf(tv.x), fabsf(tv.y)));
         }
       }
@@ -454,9 +466,10 @@ __global__ void __launch_bounds__(kThreads) prec_b_kernel(const PrecBArgs<TM, TI
             float m = tmx[rr];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if ((threadIdx.x & 31) == 0 && rr < nr && m > 0.f)
-              atomicMax(A.tmax + (long long)(r0 + rr) * A.ncl + A.leaf_cluster[leaf], __float_as_uint(m));
-            tmx[rr] = 0.f;
+            if ((threadIdx.x & 31) == 0 && rr < nr && m > 0.f) {
+              const int vid = v0 + rr, leaf = A.gleaves[grp.x + vid / A.nrhs], rhs = vid % A.nrhs;
+              atomicMax(A.tmax + (long long)rhs * A.ncl + A.leaf_cluster[leaf], __float_as_uint(m));
+            }
           }
         }
       }
@@ -530,12 +543,15 @@ cudaError_t launch_groups(const hps_handle* h, typename P::Args A, int nrhs, int
   return cudaSuccess;
 }
 
-int xcap_of(const hps_handle* h) {
-  int mx = std::max(h->nb, h->ni);
-  if (h->has_precond)
+// Shared-memory columns staged per vector: the leaf's face data (apply), its interior source
+// (right-hand side), or a cluster's internal right-hand side (stage K).
+enum class XCap { Apply, Rhs, StageK };
+int xcap_of(const hps_handle* h, XCap which) {
+  int mx = which == XCap::Apply ? h->nb : which == XCap::Rhs ? h->ni : 0;
+  if (which == XCap::StageK && h->has_precond)
     for (int c = 0; c < h->ct.ncl; ++c)
       mx = std::max(mx, (h->ct.cl_slot_begin[c + 1] - h->ct.cl_slot_begin[c]) * h->q * h->q);
-  return (int)round_up(mx, 64);
+  return (int)round_up(std::max(mx, 1), 64);
 }
 
 template <class TM, class TIN, class TOUT>
@@ -555,7 +571,7 @@ cudaError_t apply_t(const hps_handle* h, const TM* R, const TIN* f, TOUT* y, con
   A.nrhs = nrhs;
   A.nitems = (long long)h->nl * 6;
   const LaunchShape* shapes = h->shapes.apply[std::is_same<TM, double2>::value ? 1 : 0];
-  return launch_groups<P>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename P::Args& B, int r0) {
+  return launch_groups<P>(h, A, nrhs, xcap_of(h, XCap::Apply), A.q2, st, [&](typename P::Args& B, int r0) {
     B.f += (long long)r0 * h->nf;
     B.y += (long long)r0 * h->nf;
     if (B.bvec) B.bvec += (long long)r0 * h->nf;
@@ -594,6 +610,9 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.tmax = nullptr;
     A.leaf_cluster = h->dct.leaf_cluster;
     A.ncl = h->ct.ncl;
+    A.groups = h->dct.bgroups;
+    A.gleaves = h->dct.bgroup_leaves;
+    A.ngroups = (int)h->ct.bgroups.size();
     if (tc16) {
       HPS_TRY_CUDA_E(cudaMemsetAsync(h->tmax, 0, (size_t)h->ct.ncl * nrhs * sizeof(float), st));
       A.tmax = reinterpret_cast<unsigned*>(h->tmax);
@@ -606,17 +625,21 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
       int occ = 0;
       if (e2 == cudaSuccess) e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
       if (e2 != cudaSuccess) return e2;
-      const int grid = (int)std::min<long long>(h->nl, (long long)h->nsm * std::max(occ, 1));
+      const int grid = (int)std::min<long long>(A.ngroups, (long long)h->nsm * std::max(occ, 1));
       kern<<<grid, kThreads, smem, st>>>(A);
       ++h->prof.launches;
       return cudaGetLastError();
     };
-    // shared memory for NR x (the most external columns of any leaf: 3 q^2 when every
-    // cluster is 2x2x2, up to 6 q^2 for a leaf alone in its cluster)
+    // NR vectors (leaf of a group, right-hand side) per pass; shared memory for NR x (the most
+    // external columns of any leaf: 3 q^2 when every cluster is 2x2x2, up to 6 q^2 for a leaf
+    // alone in its cluster), halved while it does not fit
+    const long long nvec = (long long)std::max(h->ct.max_group, 1) * nrhs;
+    int nr = nvec <= 1 ? 1 : nvec == 2 ? 2 : nvec <= 4 ? 4 : 8;
+    while (nr > 1 && (size_t)nr * h->ct.max_ext * q2 * sizeof(Acc) + 16 > (size_t)kMaxDynSmem) nr >>= 1;
     cudaError_t e;
-    if (nrhs == 1) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 1>, 1);
-    else if (nrhs == 2) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 2>, 2);
-    else if (nrhs <= 4) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 4>, 4);
+    if (nr == 1) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 1>, 1);
+    else if (nr == 2) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 2>, 2);
+    else if (nr == 4) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 4>, 4);
     else e = launch_b(prec_b_kernel<TM, TIN, TOUT, 8>, 8);
     h->prof.end(HPS_PHASE_PRECOND_B, ev, st);
     if (e != cudaSuccess) return e;
@@ -652,7 +675,7 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     A.q2 = q2;
     A.nf = h->nf;
     A.tstride = tstride;
-    const int xcap = xcap_of(h);
+    const int xcap = xcap_of(h, XCap::StageK);
     long long* counter = &h->prof.launches;
     cudaEvent_t ev = h->prof.begin(st);
     cudaError_t e = cudaSuccess;
@@ -743,7 +766,7 @@ cudaError_t rhs_t(const hps_handle* h, const TM* H, const double2* s, const doub
   A.nrhs = nrhs;
   A.nitems = (long long)h->nl * 6;
   static const LaunchShape kDefault[4] = {{4, 0}, {4, 0}, {2, 0}, {1, 0}};
-  return launch_groups<P>(h, A, nrhs, xcap_of(h), A.q2, st, [&](typename P::Args& B, int r0) {
+  return launch_groups<P>(h, A, nrhs, xcap_of(h, XCap::Rhs), A.q2, st, [&](typename P::Args& B, int r0) {
     if (B.s) B.s += (long long)r0 * h->nint;
     if (B.t) B.t += (long long)r0 * h->nf;
     B.out += (long long)r0 * h->nf;
@@ -865,7 +888,7 @@ cudaError_t tune_apply(hps_handle* h, const TM* R, int kind, void* fbuf, void* y
   A.nitems = (long long)h->nl * 6;
   const int g = group_index(nr);
   const std::array<long long, 6> key{h->dev, kind, h->q, h->nl, nr, A.nitems};
-  h->shapes.apply[kind][g] = tune_group<P>(h, A, nr, xcap_of(h), A.q2, key, h->shapes.apply[kind][g], st);
+  h->shapes.apply[kind][g] = tune_group<P>(h, A, nr, xcap_of(h, XCap::Apply), A.q2, key, h->shapes.apply[kind][g], st);
   return cudaSuccess;
 }
 
@@ -894,7 +917,7 @@ cudaError_t tune_stage_k(hps_handle* h, const TM* K, const float* kscale, void* 
     A.nitems = n;
     A.nrhs = 1 << g;
     const std::array<long long, 6> key{h->dev, 10 + (long long)sizeof(TM), h->q, h->nl, g, n};
-    h->shapes.k[g] = tune_group<P>(h, A, 1 << g, xcap_of(h), A.q2, key, h->shapes.k[g], st);
+    h->shapes.k[g] = tune_group<P>(h, A, 1 << g, xcap_of(h, XCap::StageK), A.q2, key, h->shapes.k[g], st);
   }
   return cudaSuccess;
 }

@@ -121,6 +121,11 @@ struct ClusterTables {
   // FP16 tensor-core stage K of one right-hand side (uniform layout): items (block, 128-row
   // tile, first member position, members <= 64)
   std::vector<int4> tc16_items;
+  // stage-B work items: leaves sorted by B block, in groups of at most kBGroup that share one
+  // block (first index into bgroup_leaves, count)
+  std::vector<int> bgroup_leaves;
+  std::vector<int2> bgroups;
+  int max_group = 0;
 };
 
 struct DeviceClusterTables {
@@ -146,6 +151,8 @@ struct DeviceClusterTables {
   int* pos_class = nullptr;
   int* leaf_cluster = nullptr;
   int4* tc16_items = nullptr;
+  int* bgroup_leaves = nullptr;
+  int2* bgroups = nullptr;
 };
 
 // Launch shape of the batched GEMV kernels: matrix rows per warp pass and a cap on
@@ -421,6 +428,10 @@ constexpr int kTcMinMembers = 16;
 // Stage-K work items of the SIMT kernel cover 1/kKRowSplit of a slot's q^2 rows
 // (finer items balance the last wave of the launch).
 constexpr int kKRowSplit = 2;
+// Leaves per stage-B work item (leaves sharing one B block).
+constexpr int kBGroup = 8;
+// Dynamic shared memory a block may opt into on sm_103 (227 KB).
+constexpr int kMaxDynSmem = 227 * 1024;
 
 // ---- apply.cu ----
 // C128 complex double, C64 complex float, DF complex double-float (float4: re.h, im.h, re.l, im.l)

@@ -917,6 +917,20 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
     HPS_CUDA_TRY(cudaMemcpyAsync(k.r, b, vb, cudaMemcpyDeviceToDevice, st));
     rnorm = bnorm;
   }
+  // a residual norm that is not finite ends the solve (it would compare as converged)
+  auto finite_norms = [&](const char* where) -> int {
+    int nbad = 0, first = -1;
+    for (int r = 0; r < nrhs; ++r)
+      if (!std::isfinite(rnorm[r]) || !std::isfinite(bnorm[r])) {
+        if (first < 0) first = r;
+        ++nbad;
+      }
+    if (nbad == 0) return HPS_OK;
+    set_error(std::string("GMRES: non-finite residual norm (") + where + ", " + std::to_string(nbad) + " of " +
+              std::to_string(nrhs) + " right-hand sides, the first " + std::to_string(first) + ")");
+    return HPS_EBREAKDOWN;
+  };
+  if ((rc = finite_norms("initial residual"))) return rc;
   int its = 0, cycles = 0;
   long long nre_total = 0;
   const double eps_inner = mixed ? 1e-6 : 0.0;
@@ -1042,6 +1056,7 @@ int gmres_core(hps_handle* h, const GmresOps& ops, bool mixed, const double2* b,
     int done = 0;
     for (int r = 0; r < nrhs; ++r) done = std::max(done, hread[nrhs + r]);
     nre_total += hread[3 * nrhs + 2];
+    if ((rc = finite_norms("restart residual"))) return rc;
     if (replayed && h->prof.on) h->prof.read_recs(k.graph.recs, done);
     its += done;
     if (h->tc_error) {

@@ -258,6 +258,13 @@ __global__ void assemble_kernel(T* W, long long wstride, int ld, const int* leaf
 // [gj0, k) above them, so on exit rows [gj0, n) of columns [n, ncols) hold
 // the corresponding rows of A^{-1} E.  A zero pivot sets *status = 1.
 // ---------------------------------------------------------------------------
+// v -= m u (complex), the elimination's one update
+template <class T>
+__device__ __forceinline__ void gj_update(T& v, const T m, const T u) {
+  v.x -= m.x * u.x - m.y * u.y;
+  v.y -= m.x * u.y + m.y * u.x;
+}
+
 template <class T, int NT>
 __global__ void __launch_bounds__(NT) gj_kernel(T* W, long long wstride, int ld, int n, int ncols,
                                                 int gj0, int nbatch, int* status) {
@@ -320,11 +327,21 @@ __global__ void __launch_bounds__(NT) gj_kernel(T* W, long long wstride, int ld,
       T* Mr = M + (long long)r * ld;
       const T m = Mr[k];
       if (m.x == 0 && m.y == 0) continue;
-      for (int c = k + 1 + lane; c < ncols; c += 32) {
-        const T u = prow[c];
+      // four loads in flight per lane; every element gets the same update as one at a time
+      int c = k + 1 + lane;
+      for (; c + 96 < ncols; c += 128) {
+        T v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = Mr[c + 32 * e];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          gj_update(v[e], m, prow[c + 32 * e]);
+          Mr[c + 32 * e] = v[e];
+        }
+      }
+      for (; c < ncols; c += 32) {
         T v = Mr[c];
-        v.x -= m.x * u.x - m.y * u.y;
-        v.y -= m.x * u.y + m.y * u.x;
+        gj_update(v, m, prow[c]);
         Mr[c] = v;
       }
     }
@@ -763,10 +780,12 @@ size_t workspace_budget(const hps_handle* h) {
 
 }  // namespace
 
-// Cap on the transient setup workspace: 24 GiB, the remaining HBM budget of
-// the handle when one is set, (setup also keeps it under a third of the free device memory).
+// Cap on the transient setup workspace: 24 GiB, raised up to 96 GiB where that is needed for one
+// leaf elimination per SM (large leaves, p >= 14); the remaining HBM budget of the handle when one
+// is set (setup also keeps it under a third of the free device memory).
 size_t workspace_cap(const hps_handle* h) {
-  size_t cap = (size_t)24 << 30;
+  const size_t per = (size_t)h->n * (size_t)(h->n + h->nb + h->ni) * sizeof(double2);
+  size_t cap = std::max((size_t)24 << 30, std::min(per * (size_t)std::max(h->nsm, 1), (size_t)96 << 30));
   if (h->opt.hbm_budget) {
     const size_t rest = h->opt.hbm_budget > h->bytes ? h->opt.hbm_budget - h->bytes : 0;
     cap = std::min(cap, rest);
@@ -1109,6 +1128,21 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
         }
       }
   }
+  // stage-B groups: leaves of one B block (ascending), kBGroup at a time
+  {
+    std::vector<std::vector<int>> by_class(ct.nbc);
+    for (int leaf = 0; leaf < h->nl; ++leaf) by_class[ct.leaf_bcls[leaf]].push_back(leaf);
+    ct.bgroup_leaves.clear();
+    ct.bgroups.clear();
+    ct.max_group = 0;
+    for (const auto& ls : by_class)
+      for (size_t i = 0; i < ls.size(); i += kBGroup) {
+        const int cnt = (int)std::min<size_t>(kBGroup, ls.size() - i);
+        ct.bgroups.push_back(make_int2((int)ct.bgroup_leaves.size(), cnt));
+        ct.max_group = std::max(ct.max_group, cnt);
+        for (int g = 0; g < cnt; ++g) ct.bgroup_leaves.push_back(ls[i + g]);
+      }
+  }
   // one 3D array of blocks and one [position][nint] matrix of t (multi-RHS stage K)
   ct.pos_class.assign(ct.ncl, 0);
   for (int m = 0; m < ct.ncl; ++m) ct.pos_class[m] = ct.cl_class[ct.kc_members[m]];
@@ -1330,6 +1364,8 @@ int classify_preconditioner(hps_handle* h, const double2* cdiag, cudaStream_t st
   if ((rc = upload(h, h->dct.pos_class, ct.pos_class, st))) return rc;
   if ((rc = upload(h, h->dct.leaf_cluster, ct.leaf_cluster, st))) return rc;
   if ((rc = upload(h, h->dct.tc16_items, ct.tc16_items, st))) return rc;
+  if ((rc = upload(h, h->dct.bgroup_leaves, ct.bgroup_leaves, st))) return rc;
+  if ((rc = upload(h, h->dct.bgroups, ct.bgroups, st))) return rc;
   for (int i = 0; i < 4; ++i)
     if ((rc = upload(h, h->dct.kitems[i], ct.kitems[i], st))) return rc;
   HPS_CUDA_TRY(cudaStreamSynchronize(st));

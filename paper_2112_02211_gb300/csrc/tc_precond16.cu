@@ -107,7 +107,10 @@ __device__ __forceinline__ void decode(const Pk16Args& a, long long item, int& b
   }
 }
 
-// 1 / (largest component of t) of the cluster whose data fills B row m, 0 for unused rows
+// 1 / (largest component of t) of the cluster whose data fills B row m, 0 for unused rows.  A
+// maximum below the smallest normal float (a cluster far from every source, whose t holds only
+// subnormal values) would overflow the reciprocal: such a cluster's t is taken as 0, a change
+// below 2^-126 of the vector's scale.
 template <bool MULTI>
 __device__ __forceinline__ float inv_scale(const Pk16Args& a, int m, int pos0, int cnt, int rt) {
   float mx;
@@ -119,7 +122,7 @@ __device__ __forceinline__ float inv_scale(const Pk16Args& a, int m, int pos0, i
     if (m >= cnt) return 0.f;
     mx = a.tmax[a.members[pos0 + m]];
   }
-  return mx > 0.f ? 1.f / mx : 0.f;
+  return mx >= 0x1p-126f ? 1.f / mx : 0.f;
 }
 
 template <bool MULTI>
@@ -194,10 +197,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= 2 && warp < 8) {
     // ---------------- t -> FP16 B operand (conj rows, swap rows), 128-byte swizzle ----------------
     const int tt = threadIdx.x - 64;  // 0..191
+    constexpr int kTasks = kCols * 8, kPer = (kTasks + 191) / 192;
     long long it = 0;
     for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
       int blk, mt, pos0, cnt, rt;
       decode<MULTI>(a, item, blk, mt, pos0, cnt, rt);
+      // a thread fills the same B rows at every K step: their scales once per item
+      float scr[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int task = tt + 192 * i;
+        scr[i] = task < kTasks ? inv_scale<MULTI>(a, task >> 3, pos0, cnt, rt) : 0.f;
+      }
       for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
         const int s = (int)(it % kStages);
         const uint32_t ph = (uint32_t)((it / kStages) & 1);
@@ -210,9 +221,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned char* T = st + kABytes + kBBytes;
         // task = (row m, 16-byte chunk c of the B row): 4 complex values of K index 4c..4c+3,
         // which are floats 8(c%4)..8(c%4)+7 of T box c/4, row m (two 16-byte T chunks)
-        for (int task = tt; task < kCols * 8; task += 192) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          const int task = tt + 192 * i;
+          if (task >= kTasks) break;
           const int m = task >> 3, c = task & 7;
-          const float sc = inv_scale<MULTI>(a, m, pos0, cnt, rt);
+          const float sc = scr[i];
           const unsigned char* trow = T + (c >> 2) * kTBoxBytes + m * 128;
           const int ch0 = 2 * (c & 3);
           const float4 p0 = *reinterpret_cast<const float4*>(trow + ((ch0 ^ (m & 7)) << 4));

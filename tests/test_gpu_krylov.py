@@ -97,3 +97,18 @@ def test_profile_counts_under_graph_replay(case):
     assert p["count"]["arnoldi"] == info["iterations"]
     assert p["count"]["residual"] == info["cycles"]
     assert p["ms"]["apply"] > 0 and p["launches"] > 10 * info["iterations"]
+
+
+def test_non_finite_residual_is_an_error(case):
+    """A NaN in the data makes every residual norm NaN, which compares false against any
+    tolerance: the solve must end with HPS_EBREAKDOWN, not report convergence."""
+    w, oc, solver, s = case
+    bad = s.clone()
+    bad[7] = complex(float("nan"), 0.0)
+    for form in ("mixed", "fp64"):
+        with pytest.raises(hps.HPSError) as ei:
+            solver.solve(s=bad, tol=1e-8, form=form)
+        assert ei.value.code == -5 and "non-finite" in str(ei.value), ei.value
+    # the handle still solves
+    f, info = solver.solve(s=s, tol=1e-8, form="mixed")
+    assert info["converged"] and rel(f.cpu().numpy(), oc.solve()) < 1e-6

@@ -84,6 +84,15 @@ def test_fp16_tensor_core_stage_k(case):
     z0 = solver.precond(torch.from_numpy(r0).cuda(), fp16_blocks=True).cpu().numpy()
     assert np.all(np.isfinite(z0))
     assert rel(z0, oc.M(r0.astype(np.complex128))) < 5e-3
+    # ... or holds only subnormal floats there (a source far away): the per-cluster scale of t
+    # must not overflow; those clusters count as 0, a change far below the bar
+    rs = np.full(n, 3e-40 + 2e-40j, dtype=np.complex64)
+    rs[: oc.grid.nb] = r[0, : oc.grid.nb]
+    zs = solver.precond(torch.from_numpy(rs).cuda(), fp16_blocks=True).cpu().numpy()
+    assert np.all(np.isfinite(zs))
+    assert rel(zs, oc.M(rs.astype(np.complex128))) < 5e-3
+    zs64 = solver.precond(torch.from_numpy(np.tile(rs, 64)).cuda(), fp16_blocks=True).cpu().numpy()
+    assert np.all(np.isfinite(zs64)) and rel(zs64.reshape(64, -1)[17], zs) < 1e-6
 
 
 def test_batched_stage_b_equals_single_rhs_stage_b(case):
