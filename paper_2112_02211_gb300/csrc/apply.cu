@@ -634,12 +634,18 @@ cudaError_t precond_t(const hps_handle* h, const TM* B, const TM* K, const TIN* 
     // external columns of any leaf: 3 q^2 when every cluster is 2x2x2, up to 6 q^2 for a leaf
     // alone in its cluster), halved while it does not fit
     const long long nvec = (long long)std::max(h->ct.max_group, 1) * nrhs;
-    int nr = nvec <= 1 ? 1 : nvec == 2 ? 2 : nvec <= 4 ? 4 : 8;
+    // (32 at a time with FP32 accumulators and many right-hand sides: each B entry read from L2
+    // then feeds 32 accumulations)
+    constexpr bool kWide = sizeof(Acc) == 8;
+    int nr = nvec <= 1 ? 1 : nvec == 2 ? 2 : nvec <= 4 ? 4 : (kWide && nvec >= 32) ? 32 : 8;
     while (nr > 1 && (size_t)nr * h->ct.max_ext * q2 * sizeof(Acc) + 16 > (size_t)kMaxDynSmem) nr >>= 1;
     cudaError_t e;
     if (nr == 1) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 1>, 1);
     else if (nr == 2) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 2>, 2);
     else if (nr == 4) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 4>, 4);
+    else if (nr == 8) e = launch_b(prec_b_kernel<TM, TIN, TOUT, 8>, 8);
+    else if constexpr (kWide) e = nr == 32 ? launch_b(prec_b_kernel<TM, TIN, TOUT, 32>, 32)
+                                           : launch_b(prec_b_kernel<TM, TIN, TOUT, 16>, 16);
     else e = launch_b(prec_b_kernel<TM, TIN, TOUT, 8>, 8);
     h->prof.end(HPS_PHASE_PRECOND_B, ev, st);
     if (e != cudaSuccess) return e;

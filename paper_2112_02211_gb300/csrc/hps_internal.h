@@ -428,8 +428,11 @@ constexpr int kTcMinMembers = 16;
 // Stage-K work items of the SIMT kernel cover 1/kKRowSplit of a slot's q^2 rows
 // (finer items balance the last wave of the launch).
 constexpr int kKRowSplit = 2;
-// Leaves per stage-B work item (leaves sharing one B block).
-constexpr int kBGroup = 8;
+// Leaves per stage-B work item (leaves sharing one B block).  Items of 8 leaves were measured
+// faster (0.070 vs 0.147 ms per application at 16^3 leaves) but gave a wrong preconditioner on a
+// complex medium (GMRES stalled; the same items one vector at a time gave other iterates than
+// one leaf per item), for a reason not yet found; one leaf per item until it is.
+constexpr int kBGroup = 1;
 // Dynamic shared memory a block may opt into on sm_103 (227 KB).
 constexpr int kMaxDynSmem = 227 * 1024;
 

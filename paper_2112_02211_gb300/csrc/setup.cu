@@ -1151,7 +1151,7 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
     const long long nint0 = ct.nkc > 0 ? (long long)(ct.kc_slot_begin[1] - ct.kc_slot_begin[0]) * q2 : 0;
     if (nint0 == 0 || nint0 % 16 != 0) ct.uniform = false;
     for (int k = 0; k < ct.nkc && ct.uniform; ++k)
-      if ((long long)(ct.kc_slot_begin[k + 1] - ct.kc_slot_begin[k]) * q2 != nint0 || ct.kc_off[k] != k * nint0 * nint0)
+      if ((long long)(ct.kc_slot_begin[k + 1] - ct.kc_slot_begin[k]) * q2 != nint0 || ct.kc_off[k] != (long long)k * nint0 * nint0)
         ct.uniform = false;
     for (int m = 0; m < ct.ncl && ct.uniform; ++m)
       if (ct.cl_tpos[ct.kc_members[m]] != m * nint0) ct.uniform = false;

@@ -7,11 +7,16 @@
 //   the entries are at most 1), read by TMA as a real n x 2n matrix A of
 //   interleaved (re, im) halves: 64 halves (128 bytes) per row and stage;
 // * t of each member cluster (complex FP32, the stage-B output) divided by the
-//   largest component of that cluster's t (stage B records it), converted to
-//   FP16 by the transform warps into the rows conj(t) and the re/im swap of t,
-//   so that A B = [Re | Im] of K_c t / (s_row t_max).
-// The epilogue multiplies back by s_row and t_max.  Both operands carry 2^-11
-// relative rounding, the precision of the FP16 blocks the SIMT stage K uses.
+//   largest component of that cluster's t (stage B records it) and split by
+//   the transform warps into two FP16 terms, hi + lo (~22 bits), each laid out
+//   as the rows conj(t) and the re/im swap of t, so that A B_hi + A B_lo =
+//   [Re | Im] of K_c t / (s_row t_max).
+// The epilogue multiplies back by s_row and t_max.  K_c carries 2^-11 relative
+// rounding (a fixed matrix: the FP16 blocks the SIMT stage K uses); t is kept
+// to ~2^-22, so the result stays linear in t to FP32 level.  That matters:
+// GMRES applies the preconditioner to V y in its update and assumes that this
+// equals sum_j y_j M^{-1} v_j; one FP16 rounding of t (2^-11, input-dependent)
+// broke that and stalled restarted GMRES near 1e-4 on the 32^3-leaf workload.
 //
 // Needs the uniform layout (every cluster 2x2x2, 24 q^2 a multiple of 32):
 // the blocks are one [block][row][2n halves] array and t one
@@ -21,10 +26,11 @@
 // * 64, 128, ... right-hand sides: (position, 128-row tile, 64-RHS tile); B
 //   rows = right-hand sides of one member.
 //
-// Warp roles (384 threads, one CTA per SM, persistent): warp 0 TMA producer
-// (A tile 128 rows x 128 bytes, two T boxes of 32 floats x 64 rows), warp 1
-// TMEM allocation and the MMA issuer, warps 2..7 the FP16 conversion of t into
-// the swizzled B tile, warps 8..11 the epilogue.  Every wait is bounded; on a
+// Warp roles (384 threads, one CTA per SM, persistent, three 64 KB stages):
+// warp 0 TMA producer (A tile 128 rows x 128 bytes, two T boxes of 32 floats x
+// 64 rows), warp 1 TMEM allocation and the MMA issuer (two MMAs per K chunk:
+// hi and lo), warps 2..7 the FP16 conversion of t into the two swizzled B
+// tiles, warps 8..11 the epilogue.  Every wait is bounded; on a
 // time-out the CTA sets the error word, waits (bounded) for its own copies and
 // MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -43,7 +49,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kTileM = 128;
 constexpr int kCols = 64;               // B rows per operand half: members or right-hand sides
 constexpr int kTileN = 2 * kCols;       // (re, im) accumulator columns
@@ -51,8 +57,10 @@ constexpr int kKHalves = 64;            // K extent of a stage (128 bytes of FP1
 constexpr int kABytes = kTileM * 128;   // 16 KB
 constexpr int kBBytes = kTileN * 128;   // 16 KB
 constexpr int kTBoxBytes = kCols * 128; // 8 KB: 64 rows x 32 floats
-// stage layout (1024-byte aligned parts): A | B | T box 0 | T box 1
-constexpr int kStageBytes = kABytes + kBBytes + 2 * kTBoxBytes;  // 48 KB
+// stage layout (1024-byte aligned parts): A | B (high halves of t) | B (low halves) | T box 0 |
+// T box 1
+constexpr int kTOff = kABytes + 2 * kBBytes;
+constexpr int kStageBytes = kTOff + 2 * kTBoxBytes;  // 64 KB
 constexpr int kThreads = 384;
 constexpr int kTmemCols = 256;
 
@@ -183,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char* st = ring + s * kStageBytes;
           mbar_expect_tx(&bars->full[s], kABytes + 2 * kTBoxBytes);
           tma_load_3d(st, &mapA, &bars->full[s], kb * kKHalves, mt * kTileM, blk);
-          unsigned char* tdst = st + kABytes + kBBytes;
+          unsigned char* tdst = st + kTOff;
           for (int b = 0; b < 2; ++b) {
             const int x = kb * kKHalves + b * 32;  // floats of t: the same K range as the halves of A
             if (MULTI) tma_load_3d(tdst + b * kTBoxBytes, &mapT, &bars->full[s], x, pos0, rt * kCols);
@@ -218,7 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         unsigned char* st = ring + s * kStageBytes;
         unsigned char* B = st + kABytes;
-        const unsigned char* T = st + kABytes + kBBytes;
+        unsigned char* Blo = B + kBBytes;
+        const unsigned char* T = st + kTOff;
         // task = (row m, 16-byte chunk c of the B row): 4 complex values of K index 4c..4c+3,
         // which are floats 8(c%4)..8(c%4)+7 of T box c/4, row m (two 16-byte T chunks)
 #pragma unroll
@@ -231,22 +240,29 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int ch0 = 2 * (c & 3);
           const float4 p0 = *reinterpret_cast<const float4*>(trow + ((ch0 ^ (m & 7)) << 4));
           const float4 p1 = *reinterpret_cast<const float4*>(trow + (((ch0 + 1) ^ (m & 7)) << 4));
-          const __half2 c0 = __floats2half2_rn(p0.x * sc, -p0.y * sc), c1 = __floats2half2_rn(p0.z * sc, -p0.w * sc);
-          const __half2 c2 = __floats2half2_rn(p1.x * sc, -p1.y * sc), c3 = __floats2half2_rn(p1.z * sc, -p1.w * sc);
-          const __half2 w0 = __floats2half2_rn(p0.y * sc, p0.x * sc), w1 = __floats2half2_rn(p0.w * sc, p0.z * sc);
-          const __half2 w2 = __floats2half2_rn(p1.y * sc, p1.x * sc), w3 = __floats2half2_rn(p1.w * sc, p1.z * sc);
-          uint4 cj, sw;
-          cj.x = *reinterpret_cast<const uint32_t*>(&c0);
-          cj.y = *reinterpret_cast<const uint32_t*>(&c1);
-          cj.z = *reinterpret_cast<const uint32_t*>(&c2);
-          cj.w = *reinterpret_cast<const uint32_t*>(&c3);
-          sw.x = *reinterpret_cast<const uint32_t*>(&w0);
-          sw.y = *reinterpret_cast<const uint32_t*>(&w1);
-          sw.z = *reinterpret_cast<const uint32_t*>(&w2);
-          sw.w = *reinterpret_cast<const uint32_t*>(&w3);
+          // t / t_max = hi + lo in two FP16 terms (~22 bits): the product stays linear in t to
+          // FP32 level, as the Krylov update, which applies the preconditioner to V y, needs
+          const float x[8] = {p0.x * sc, p0.y * sc, p0.z * sc, p0.w * sc, p1.x * sc, p1.y * sc, p1.z * sc, p1.w * sc};
+          uint32_t cjh[4], swh[4], cjl[4], swl[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const __half2 h = __floats2half2_rn(x[2 * e], x[2 * e + 1]);  // (re, im) high parts
+            const __half2 l = __floats2half2_rn(x[2 * e] - __low2float(h), x[2 * e + 1] - __high2float(h));
+            // conj row (re, -im), swap row (im, re); negation is exact in FP16
+            const __half2 hc = __halves2half2(__low2half(h), __hneg(__high2half(h)));
+            const __half2 hs = __halves2half2(__high2half(h), __low2half(h));
+            const __half2 lc = __halves2half2(__low2half(l), __hneg(__high2half(l)));
+            const __half2 ls = __halves2half2(__high2half(l), __low2half(l));
+            cjh[e] = *reinterpret_cast<const uint32_t*>(&hc);
+            swh[e] = *reinterpret_cast<const uint32_t*>(&hs);
+            cjl[e] = *reinterpret_cast<const uint32_t*>(&lc);
+            swl[e] = *reinterpret_cast<const uint32_t*>(&ls);
+          }
           const int pc = (c ^ (m & 7)) << 4;  // rows m and 64 + m share the swizzle phase
-          *reinterpret_cast<uint4*>(B + m * 128 + pc) = cj;
-          *reinterpret_cast<uint4*>(B + (kCols + m) * 128 + pc) = sw;
+          *reinterpret_cast<uint4*>(B + m * 128 + pc) = make_uint4(cjh[0], cjh[1], cjh[2], cjh[3]);
+          *reinterpret_cast<uint4*>(B + (kCols + m) * 128 + pc) = make_uint4(swh[0], swh[1], swh[2], swh[3]);
+          *reinterpret_cast<uint4*>(Blo + m * 128 + pc) = make_uint4(cjl[0], cjl[1], cjl[2], cjl[3]);
+          *reinterpret_cast<uint4*>(Blo + (kCols + m) * 128 + pc) = make_uint4(swl[0], swl[1], swl[2], swl[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -280,11 +296,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t base = smem_u32(ring + s * kStageBytes);
-          const uint32_t aa = base, bb = base + kABytes;
+          const uint32_t aa = base, bb = base + kABytes, bl = bb + kBBytes;
 #pragma unroll
           for (int kk = 0; kk < kKHalves / 16; ++kk) {
             const uint32_t off = kk * 32;  // 16 halves
             mma_f16(acc, smem_desc(aa + off), smem_desc(bb + off), idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+            mma_f16(acc, smem_desc(aa + off), smem_desc(bl + off), idesc, 1u);
           }
           mma_commit(&bars->empty[s]);
         }

@@ -64,8 +64,9 @@ def test_batched_precond_matches_oracle_and_single_rhs(case):
 def test_fp16_tensor_core_stage_k(case):
     """The preconditioner with FP16 blocks (the mixed solve's) runs stage K for every cluster on
     the tensor cores with FP16 operands: K_c's FP16 copy against t scaled per cluster by its
-    largest component (stage B records it).  Both operands carry 2^-11 relative rounding, the
-    FP16 blocks' own precision: against the oracle's preconditioner at 5e-3.  With 64
+    largest component (stage B records it) and split into two FP16 terms.  K_c carries 2^-11
+    relative rounding, the FP16 blocks' own precision: against the oracle's preconditioner at
+    5e-3.  With 64
     right-hand sides the same products are tiled by (member, right-hand side) instead of by
     members: each right-hand side equals its single-RHS result to 1e-6."""
     w, oc, solver, _ = case
@@ -78,6 +79,13 @@ def test_fp16_tensor_core_stage_k(case):
         zk = solver.precond(rd[k * n:(k + 1) * n].clone(), fp16_blocks=True).cpu().numpy()
         assert rel(zk, oc.M(r[k].astype(np.complex128))) < 5e-3, k
         assert rel(z64[k], zk) < 1e-6, k
+    # linear in r to FP32 level: GMRES applies the preconditioner to V y in its update and
+    # assumes M^{-1}(V y) = sum_j y_j M^{-1} v_j.  t enters the FP16 products as two FP16 terms
+    # (~2^-22); one FP16 rounding of t (2^-11, input-dependent) gave ~2e-4 here
+    zx = solver.precond(rd[n:2 * n].clone(), fp16_blocks=True).cpu().numpy()
+    zy = solver.precond(rd[2 * n:3 * n].clone(), fp16_blocks=True).cpu().numpy()
+    zxy = solver.precond((rd[n:2 * n] + 0.5 * rd[2 * n:3 * n]).contiguous(), fp16_blocks=True).cpu().numpy()
+    assert rel(zxy, zx + 0.5 * zy) < 3e-5
     # a right-hand side that vanishes on some clusters: their z_int is exactly 0
     r0 = np.zeros(n, dtype=np.complex64)
     r0[: oc.grid.nb] = r[0, : oc.grid.nb]
