@@ -369,10 +369,10 @@ def run_gpu(args, dist):
     rpw = shapes["apply_rows_per_warp"][0][0]
     kernels = {"apply": f"seg_gemv_kernel<ApplyP<float2,float2,float4>,1,{rpw}> (rows per warp chosen at setup)",
                "precond_k": "tc_precond16_kernel<false> (every cluster block on the tensor cores, kind::f16, "
-                            "t scaled per cluster) when the clusters are uniform, else "
+                            "t scaled per cluster as two FP16 terms) when the clusters are uniform, else "
                             "seg_gemv_kernel<PrecKP<__half2,float2,float2>,1,R>",
-               "precond_b": "prec_b_kernel<__half2,float4,float2,8> (8 leaves sharing a B block per item, "
-                            "one thread per row)"}
+               "precond_b": "prec_b_kernel<__half2,float4,float2,1> (one leaf per item, one thread per row, "
+                            "B transposed)"}
     roof = {}
     for ph, by in phases.items():
         cnt = prof["count"][ph]
@@ -516,6 +516,7 @@ def run_config(name, dist):
         ms = e0.elapsed_time(e1) / steps
         prof = solver.profile(enable=False, reset=True)
         ncl, k_blocks, b_blocks = solver.precond_info()
+        shapes = solver.launch_shapes()
         mem = solver.memory_bytes
         nf = solver.nf
     finally:
@@ -570,7 +571,8 @@ def run_config(name, dist):
             "iterations": info["iterations"], "cycles": info["cycles"], "rel_residual": info["rel_residual"],
             "converged": info["converged"], "reorth_steps": info["reorth_steps"],
             "phase_ms_per_solve": {k: round(v / steps, 3) for k, v in prof["ms"].items()},
-            "gpu_launches_per_solve": prof["launches"] // steps, "roofline": roof, "peak_sources": [pk_src, tpk_src]}
+            "gpu_launches_per_solve": prof["launches"] // steps, "roofline": roof, "peak_sources": [pk_src, tpk_src],
+            "launch_shapes": shapes}
 
 
 def run_serving(args, dist):

@@ -1128,10 +1128,11 @@ void assign_blocks(hps_handle* h, const std::vector<double2>* lamq) {
         }
       }
   }
-  // stage-B groups: leaves of one B block (ascending), kBGroup at a time
+  // stage-B groups: leaves of one B block (ascending), kBGroup at a time; with one leaf per
+  // group, in leaf order (neighbouring leaves on neighbouring CTAs write neighbouring t slots)
   {
-    std::vector<std::vector<int>> by_class(ct.nbc);
-    for (int leaf = 0; leaf < h->nl; ++leaf) by_class[ct.leaf_bcls[leaf]].push_back(leaf);
+    std::vector<std::vector<int>> by_class(kBGroup > 1 ? ct.nbc : 1);
+    for (int leaf = 0; leaf < h->nl; ++leaf) by_class[kBGroup > 1 ? ct.leaf_bcls[leaf] : 0].push_back(leaf);
     ct.bgroup_leaves.clear();
     ct.bgroups.clear();
     ct.max_group = 0;

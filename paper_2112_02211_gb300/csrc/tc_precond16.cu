@@ -13,10 +13,10 @@
 //   [Re | Im] of K_c t / (s_row t_max).
 // The epilogue multiplies back by s_row and t_max.  K_c carries 2^-11 relative
 // rounding (a fixed matrix: the FP16 blocks the SIMT stage K uses); t is kept
-// to ~2^-22, so the result stays linear in t to FP32 level.  That matters:
-// GMRES applies the preconditioner to V y in its update and assumes that this
-// equals sum_j y_j M^{-1} v_j; one FP16 rounding of t (2^-11, input-dependent)
-// broke that and stalled restarted GMRES near 1e-4 on the 32^3-leaf workload.
+// to ~2^-22, so the result stays linear in t to FP32 level.  GMRES applies the
+// preconditioner to V y in its update and assumes that this equals
+// sum_j y_j M^{-1} v_j; with one FP16 rounding of t (2^-11, input-dependent)
+// that would hold only to ~2e-4.
 //
 // Needs the uniform layout (every cluster 2x2x2, 24 q^2 a multiple of 32):
 // the blocks are one [block][row][2n halves] array and t one
