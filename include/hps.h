@@ -260,6 +260,12 @@ int hps_rhs(hps_handle* h, const double* s, const double* t, int nrhs, double* b
  * pass cancelled most of the vector (Rutishauser's criterion, ||w'|| <
  * ||w||/10, which bounds the loss of orthogonality per step by ~10 eps);
  * HPS_SOLVE_CGS2 forces the second pass everywhere.
+ *
+ * Errors: HPS_ENOCONV when maxit iterations did not reach tol (f_out holds
+ * the last iterate, info the last residual); HPS_EBREAKDOWN when a residual
+ * norm is not finite (NaN or Inf in the data or a non-finite intermediate),
+ * found at the start or at a restart; HPS_ETIMEOUT when a tensor-core
+ * kernel's bounded wait gave up; HPS_ECUDA for a CUDA error.
  */
 int hps_gmres_solve(hps_handle* h, int form, const double* s, const double* t, int nrhs,
                     double tol, double* f_out, hps_solve_info* info, void* stream);
